@@ -1,0 +1,264 @@
+/*
+ * ising.h — C ABI of the GB300-native Ising-film Monte Carlo library.
+ *
+ * The library runs the checkerboard single-spin-flip Metropolis sweep of the
+ * nearest-neighbour Ising model on an Lx x Ly x Lz simple-cubic film (Block,
+ * Kim, Virnau & Binder, arXiv:1411.5588) and the integer observable sums that
+ * feed the paper's thermodynamic integrations, entirely in CUDA kernels for
+ * sm_103a.  Nothing here takes a framework type: arguments are plain values,
+ * host pointers (marked "host") or device pointers (marked "device").
+ *
+ * Model (Eq. 1, Sec. II A):
+ *   E = -J sum_<ij> S_i S_j - H sum_i S_i - H1 sum_{kx=1} S_i - Hn sum_{kx=Lx} S_i,
+ *   Hn = -H1, S_i = +-1, sites (kx,ky,kz) with 1-based indices.
+ *   x: free surfaces at kx = 1 and kx = Lx (ISING_X_PBC is a test geometry).
+ *   z: periodic.
+ *   y: ISING_Y_GAPBC, the generalized antiperiodic rule of Eq. 11,
+ *      S(kx, ky +- Ly, kz) = -S(Lx+1-kx, ky, kz); ISING_Y_PBC and ISING_Y_APBC
+ *      are the plain periodic / antiperiodic films of Sec. II C (Eq. 20).
+ *
+ * Dynamics (Appendix: checkerboard update; the rule itself is Metropolis):
+ *   one sweep = four phases, colour c = (kx+ky+kz) mod 2:
+ *   {c=0, ky<Ly}, {c=0, ky=Ly}, {c=1, ky<Ly}, {c=1, ky=Ly}.
+ *   A site flips iff dE <= 0 or u < floor(exp(-dE/T) * 2^32), with
+ *   dE = 2 s (J sigma + h) in binary64 (h = H, += H1 on kx=1, += Hn on kx=Lx)
+ *   and u word (z0>>1)&3 of Philox4x32-10 with counter
+ *   (row = (kx-1)*Ly + (ky-1), z0>>3, sweep, z0&1), z0 = kz-1, key
+ *   (lo32(seed) ^ hi32(seed), replica).  Sweeps are numbered from 0 and must
+ *   stay below 0xFFFFFFFF.  Initial states draw from counter
+ *   (row, z0>>3, 0xFFFFFFFF, 2 | (z0&1)).
+ *
+ * Records (Eqs. 1, 7, 9, 17, 19): one record is 5 + Lx int64,
+ *   {sweeps completed, B, M, M1, Mn, m(1), ..., m(Lx)}, where
+ *   B = sum over bonds of sigma_b S_i S_j (sigma_b = -1 on the antiperiodic
+ *   wrap bonds; a pair joined through two neighbour slots, e.g. Lz = 2,
+ *   counts twice), M = sum S, M1 = m(1), Mn = m(Lx) and m(kx) is the sum of
+ *   layer kx.  The energy is E = -J B - H M - H1 M1 - Hn Mn.
+ *
+ * Memory: the library owns every device buffer it allocates; callers own
+ * every pointer they pass.  Spins are bit-packed on the device (1 bit per
+ * site).  Host spin arrays use the canonical int8 order
+ * ((kx-1)*Ly + (ky-1))*Lz + (kz-1), values +1 / -1.
+ *
+ * Errors: every call returns an ISING_* status; nothing aborts, and no
+ * kernel traps.  ising_last_error() gives a one-line message for the calling
+ * thread.  Device waits inside the library are bounded and report
+ * ISING_ETIMEOUT.  A handle may be used from one host thread at a time.
+ */
+#ifndef ISING_GB300_H
+#define ISING_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ISING_OK = 0,
+    ISING_EINVAL = 1,   /* bad argument or unsupported size */
+    ISING_ENOMEM = 2,   /* device or host allocation failed / budget exceeded */
+    ISING_ECUDA = 3,    /* a CUDA runtime call failed */
+    ISING_ETIMEOUT = 4, /* a bounded wait ran out */
+    ISING_EBUSY = 5,    /* the object is in use (e.g. jobs still running) */
+    ISING_ENOTFOUND = 6 /* unknown ticket / job */
+};
+
+enum { ISING_Y_GAPBC = 0, ISING_Y_PBC = 1, ISING_Y_APBC = 2 };
+enum { ISING_X_FREE = 0, ISING_X_PBC = 1 };
+enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
+
+typedef struct ising ising;
+
+/* ------------------------------------------------------------ one film */
+
+/* Create a film on the current CUDA device (Eq. 1, Sec. II A).
+ * Lx >= 1, Ly >= 2, Lz >= 2 and even, T > 0 (T = +inf means beta = 0).
+ * Starts all spins +1, y = GAPBC, x free, H = 0, replica 0, sweep 0.
+ * *out receives the handle (host pointer).  EINVAL / ENOMEM / ECUDA. */
+int ising_create(int Lx, int Ly, int Lz, double J, double H1, double T, uint64_t seed, ising **out);
+
+/* Boundary modes, bulk field H and RNG replica index (key word 1).
+ * x_mode = ISING_X_PBC needs Lx even.  Resets nothing else.  EINVAL. */
+int ising_set_options(ising *h, int y_mode, int x_mode, double H, uint32_t replica);
+
+/* Change the temperature (T > 0 or +inf) and the surface field H1 of Eq. 1;
+ * rebuilds the acceptance thresholds.  EINVAL. */
+int ising_set_params(ising *h, double J, double H1, double T);
+
+/* Stream used for every launch and copy of this handle (a cudaStream_t
+ * passed as void*; NULL = the library's own stream).  The caller keeps the
+ * stream alive while the handle uses it. */
+int ising_set_stream(ising *h, void *cuda_stream);
+
+/* Initial state, drawn on the device: RANDOM (S = +1 iff u < 2^31), SLAB_Y
+ * (S = +1 for ky <= Ly/2 else -1, then each spin reversed iff
+ * u < floor(flip_p 2^32), 0 <= flip_p <= 1) or ALL_UP.  Sets sweep = 0 and
+ * drops pending records. */
+int ising_init(ising *h, int kind, double flip_p);
+
+/* Copy spins from host memory s (Lx*Ly*Lz int8, canonical order, values +-1;
+ * any value > 0 reads as +1).  Stream-ordered; returns after the copy. */
+int ising_set_spins(ising *h, const int8_t *s);
+
+/* Copy spins to host memory s (Lx*Ly*Lz int8, canonical order). Synchronises. */
+int ising_get_spins(ising *h, int8_t *s);
+
+/* Device-pointer variants: s is device memory of Lx*Ly*Lz int8. Async. */
+int ising_set_spins_device(ising *h, const int8_t *s);
+int ising_get_spins_device(ising *h, int8_t *s);
+
+/* Packed state exchange (device pointers): the library's own layout, of
+ * ising_packed_words() uint32 words.  Async.  For checkpoints. */
+size_t ising_packed_words(const ising *h);
+int ising_get_packed_device(ising *h, uint32_t *dst);
+int ising_set_packed_device(ising *h, const uint32_t *src);
+
+/* Sweep counter (sweeps completed).  Setting it (with the spins) resumes a
+ * chain bit-exactly; it must stay below 0xFFFFFFFF. */
+int ising_get_sweep(const ising *h, uint64_t *sweep);
+int ising_set_sweep(ising *h, uint64_t sweep);
+
+/* Enqueue n_sweeps sweeps on the handle's stream (asynchronous).  After every
+ * sweep whose count of completed sweeps is a multiple of measure_every (> 0)
+ * one record is appended to the handle's device-side series; 0 = no records.
+ * EINVAL if the counter would reach 0xFFFFFFFF, ENOMEM if the series cannot
+ * grow. */
+int ising_sweep(ising *h, uint64_t n_sweeps, uint32_t measure_every);
+
+/* Measure the current state: synchronises, then fills *out.  m_x (host,
+ * caller-owned, Lx int64) receives the layer sums m(kx) when non-NULL. */
+typedef struct {
+    uint64_t sweep;
+    int64_t bond_sum; /* B */
+    int64_t M, M1, Mn;
+    int64_t *m_x;
+} ising_obs;
+int ising_measure(ising *h, ising_obs *out);
+
+/* Drain up to cap pending records (5 + Lx int64 each, oldest first) into
+ * host memory buf; *n_records receives the number copied.  Synchronises. */
+int ising_read_series(ising *h, int64_t *buf, size_t cap, size_t *n_records);
+
+/* Number of records waiting in the series. */
+int ising_pending_records(const ising *h, size_t *n_records);
+
+/* Block until all work of the handle is done (bounded by timeout_s;
+ * ETIMEOUT otherwise). */
+int ising_synchronize(ising *h, double timeout_s);
+
+int ising_destroy(ising *h);
+
+/* ------------------------------------------------- batches of replicas */
+
+/* One job = one independent film with its own parameters and RNG key
+ * (the many-H1/T integration points of Sec. II C, Eqs. 9, 19, 22). */
+typedef struct {
+    int32_t Lx, Ly, Lz;
+    int32_t y_mode, x_mode;
+    int32_t init_kind;     /* ISING_INIT_* */
+    double J, H, H1, T;
+    double flip_p;         /* SLAB_Y flips */
+    uint64_t seed;
+    uint32_t replica;
+    uint32_t measure_every; /* 0 = no records */
+    uint64_t n_sweeps;      /* used by the server; ignored by ising_batch_sweep */
+} ising_job;
+
+typedef struct ising_batch ising_batch;
+
+/* Allocate and initialise n films updated together: every launch of a
+ * batch covers all of its films.  jobs: host array of n.  EINVAL / ENOMEM. */
+int ising_batch_create(const ising_job *jobs, size_t n, ising_batch **out);
+int ising_batch_set_stream(ising_batch *b, void *cuda_stream);
+
+/* Enqueue n_sweeps sweeps of every film (asynchronous).  Records follow each
+ * job's measure_every.  use_graph != 0 captures the sweep chunk in a CUDA
+ * graph once and replays it. */
+int ising_batch_sweep(ising_batch *b, uint64_t n_sweeps, int use_graph);
+
+/* Per-film accessors (index i < n).  Host buffers; synchronise. */
+int ising_batch_get_spins(ising_batch *b, size_t i, int8_t *s);
+int ising_batch_read_series(ising_batch *b, size_t i, int64_t *buf, size_t cap, size_t *n_records);
+int ising_batch_synchronize(ising_batch *b, double timeout_s);
+int ising_batch_destroy(ising_batch *b);
+
+/* ------------------------------------------- continuous-batching server */
+
+typedef struct ising_server ising_server;
+typedef uint64_t ising_ticket;
+
+/* A server owns a device pool of at most hbm_budget_bytes and a host thread
+ * that runs chunks of chunk_sweeps sweeps over every admitted job, admits
+ * queued jobs whenever their packed lattice and record series fit in the
+ * pool, and retires finished jobs.  A job's result is identical whether it
+ * runs alone or among others (its RNG stream depends only on its own key). */
+int ising_server_create(size_t hbm_budget_bytes, uint32_t chunk_sweeps, ising_server **out);
+
+/* Queue jobs (host array of n); *first receives the ticket of jobs[0], the
+ * others follow consecutively.  EINVAL if a job can never fit the budget. */
+int ising_batch_submit(ising_server *s, const ising_job *jobs, size_t n, ising_ticket *first);
+
+/* *done = 1 once the job's sweeps are finished and its result is ready. */
+int ising_batch_poll(ising_server *s, ising_ticket t, int *done);
+
+/* Wait for one job (bounded; ETIMEOUT otherwise). */
+int ising_batch_wait(ising_server *s, ising_ticket t, double timeout_s);
+
+/* Result of a finished job: its records (host buf, cap records of 5 + Lx
+ * int64) and its final spins (host, may be NULL).  Timing in seconds since
+ * the server started: submit, admit and finish.  Frees the job's slot. */
+typedef struct {
+    double t_submit, t_admit, t_finish;
+    uint64_t n_records;
+} ising_job_info;
+int ising_batch_result(ising_server *s, ising_ticket t, int64_t *buf, size_t cap, int8_t *spins,
+                       ising_job_info *info);
+
+/* Pool statistics: bytes in use, jobs queued / running / finished, chunks run. */
+typedef struct {
+    size_t bytes_in_use, bytes_budget;
+    uint64_t queued, running, finished, chunks;
+    uint64_t attempts; /* spin-flip attempts done so far */
+} ising_server_stats;
+int ising_server_get_stats(ising_server *s, ising_server_stats *st);
+int ising_server_destroy(ising_server *s);
+
+/* ------------------------------------------- host FP64 integration */
+
+/* Gauss-Legendre nodes and weights on [a, b] (n >= 1), Newton iteration on
+ * P_n.  x, w: host arrays of n. */
+int ising_gauss_legendre(int n, double a, double b, double *x, double *w);
+
+/* Mean of records[k*stride + col] over k = first..n-1 (exact integer sum,
+ * then one division).  records: host. */
+int ising_series_mean(const int64_t *records, size_t n, size_t stride, size_t col, size_t first,
+                      double *mean);
+
+/* Eq. 9 as read for the literal Hamiltonian (Hn = -H1 in Eq. 1):
+ * delta_f1(H1) = -integral_0^{H1} (m_1 - m_n) dH1' from n Gauss-Legendre
+ * nodes on [0, H1]; m1[i], mn[i] are the per-site surface magnetisations at
+ * node i.  host. */
+int ising_ti_surface_field(int n, double H1, const double *m1, const double *mn, double *delta_f1);
+
+/* Eq. 19: beta F(beta_b) - beta F(beta_a) = integral U dbeta by the
+ * trapezoid rule over n points (beta[i], U[i]), beta ascending or
+ * descending.  host. */
+int ising_ti_beta_trapezoid(int n, const double *beta, const double *U, double *out);
+
+/* Eq. 19 written over T: integral U dbeta = -integral U / T^2 dT, trapezoid
+ * in T over n points (T[i], U[i]).  host. */
+int ising_ti_temperature_trapezoid(int n, const double *T, const double *U, double *out);
+
+/* ------------------------------------------------------------- misc */
+
+const char *ising_strerror(int status);
+const char *ising_last_error(void);
+/* Library version and the compute capability it was built for (e.g. 103). */
+int ising_version(int *major, int *minor, int *sm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISING_GB300_H */

@@ -1,0 +1,44 @@
+"""Thermodynamic-integration arithmetic of the paper -- TEST INFRASTRUCTURE ONLY.
+
+Plain numpy restatement, independent of the product's C implementation:
+  Eq. 9  (Sec. II A): delta_f1 = -integral_0^{H1} [m_1 + m_n] dH1'.  With
+         Hn = -H1 written literally into Eq. 1, dF/dH1 = -<M1> + <Mn>, so the
+         integrand in terms of the measured layer sums is m_1 - m_n (m_n taken
+         with the sign of its own field Hn = -H1 gives the paper's m_1 + m_n).
+  Eq. 19 (Sec. II C): beta F(beta) - beta0 F(beta0) = integral U dbeta, by the
+         trapezoid rule in beta, or over T as -integral U / T^2 dT.
+Gauss-Legendre nodes come from numpy's library routine.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def gauss_legendre(n, a, b):
+    t, w = np.polynomial.legendre.leggauss(int(n))
+    half, mid = 0.5 * (b - a), 0.5 * (b + a)
+    return mid + half * t, half * w
+
+
+def series_mean(records, col, first=0):
+    """Exact integer mean of one record column (Python integers, one division)."""
+    vals = [int(v) for v in np.asarray(records)[first:, col]]
+    return float(sum(vals)) / len(vals) if len(vals) < 2 ** 53 else sum(vals) / len(vals)
+
+
+def surface_field_ti(H1, m1, mn):
+    """Eq. 9 over Gauss-Legendre nodes on [0, H1] (m1, mn per site at each node)."""
+    x, w = gauss_legendre(len(m1), 0.0, H1)
+    return -float(np.sum(w * (np.asarray(m1, dtype=np.float64) - np.asarray(mn, dtype=np.float64))))
+
+
+def beta_trapezoid(beta, U):
+    b = np.asarray(beta, dtype=np.float64)
+    u = np.asarray(U, dtype=np.float64)
+    return float(np.sum(0.5 * (b[1:] - b[:-1]) * (u[1:] + u[:-1])))
+
+
+def temperature_trapezoid(T, U):
+    t = np.asarray(T, dtype=np.float64)
+    g = np.asarray(U, dtype=np.float64) / t ** 2
+    return -float(np.sum(0.5 * (t[1:] - t[:-1]) * (g[1:] + g[:-1])))

@@ -1,0 +1,576 @@
+// C ABI of the Ising-film library: single films and static batches.
+//
+// Everything numerical runs in the CUDA kernels of ising_kernels.cu; this file
+// validates arguments, owns device memory, builds the Metropolis threshold
+// tables of Eq. 1 and enqueues launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "ising_host.h"
+
+namespace isg {
+
+namespace {
+thread_local std::string g_err;
+}
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+const char* last_error() { return g_err.c_str(); }
+
+int check_film(int Lx, int Ly, int Lz, double T, int y_mode, int x_mode) {
+  if (Lx < 1) return fail(ISING_EINVAL, "Lx must be >= 1 (got %d)", Lx);
+  if (Ly < 2) return fail(ISING_EINVAL, "Ly must be >= 2 (got %d)", Ly);
+  if (Lz < 2 || (Lz & 1)) return fail(ISING_EINVAL, "Lz must be even and >= 2 (got %d)", Lz);
+  if (!(T > 0.0)) return fail(ISING_EINVAL, "T must be > 0 (got %g)", T);
+  if (y_mode < ISING_Y_GAPBC || y_mode > ISING_Y_APBC) return fail(ISING_EINVAL, "bad y_mode %d", y_mode);
+  if (x_mode != ISING_X_FREE && x_mode != ISING_X_PBC) return fail(ISING_EINVAL, "bad x_mode %d", x_mode);
+  if (x_mode == ISING_X_PBC && (Lx < 2 || (Lx & 1))) return fail(ISING_EINVAL, "periodic x needs even Lx >= 2");
+  const double words = 2.0 * Lx * (double)Ly * ((Lz / 2 + 31) / 32);
+  if ((double)Lx * Ly > 4.0e9 || words > 8.0e9) return fail(ISING_EINVAL, "film too large");
+  return ISING_OK;
+}
+
+void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, uint64_t seed, uint32_t replica) {
+  d.Lx = (uint32_t)Lx;
+  d.Ly = (uint32_t)Ly;
+  d.Lz = (uint32_t)Lz;
+  d.n = (uint32_t)Lz / 2;
+  d.W = (d.n + 31) / 32;
+  const uint32_t r = d.n - 32 * (d.W - 1);  // valid sites of the last word, 1..32
+  uint32_t mask = 0;
+  for (uint32_t l = 0; l < r; l++) mask |= 1u << bitpos(l);
+  d.last_mask = mask;
+  d.last_calls = (r + 3) / 4;
+  d.y_mode = (uint32_t)y_mode;
+  d.x_pbc = x_mode == ISING_X_PBC ? 1u : 0u;
+  d.key0 = (uint32_t)seed ^ (uint32_t)(seed >> 32);
+  d.key1 = replica;
+  d.upd_items = d.Lx * (d.Ly - 1) * d.W;
+  d.meas_bpl = std::max<uint32_t>(1, (d.Ly * d.W + kMeasureItemsPerBlock - 1) / kMeasureItemsPerBlock);
+  d.active = 1;
+  d.sweep_end = 0xFFFFFFFFu;
+}
+
+void build_tables(FilmDesc& d, double J, double H, double H1, double T) {
+  const int Lx = (int)d.Lx;
+  for (int cls = 0; cls < 4; cls++) {
+    const bool first = cls & 1, lastl = (cls & 2) != 0;
+    uint32_t always = 0;
+    // classes that cannot occur for this Lx keep a harmless table
+    const int n_nb = 6 - (d.x_pbc ? 0 : ((first ? 1 : 0) + (lastl ? 1 : 0)));
+    double h = H;
+    if (first) h += H1;
+    if (lastl) h += -H1;
+    for (int idx = 0; idx < 16; idx++) {
+      const int sbit = idx & 1, nal = idx >> 1;
+      d.thr[cls][idx] = 0;
+      if (nal > n_nb) continue;
+      const int s = sbit ? 1 : -1;
+      const int sigma = s * (2 * nal - n_nb);  // sum of the neighbour spins
+      const double dE = 2.0 * (double)s * (J * (double)sigma + h);
+      if (dE <= 0.0) {
+        always |= 1u << idx;
+        continue;
+      }
+      const double t = std::floor(std::ldexp(std::exp(-dE / T), 32));
+      if (t >= 4294967296.0) {
+        always |= 1u << idx;
+        continue;
+      }
+      d.thr[cls][idx] = (uint32_t)t;
+    }
+    d.always[cls] = always;
+    (void)Lx;
+  }
+}
+
+// ------------------------------------------------------------ FilmSet
+
+int FilmSet::init_device() {
+  ISG_CK(cudaGetDevice(&device));
+  ISG_CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device));
+  upd_per_sm = update_blocks_per_sm();
+  meas_per_sm = measure_blocks_per_sm();
+  if (upd_per_sm <= 0 || meas_per_sm <= 0) return fail(ISING_ECUDA, "occupancy query failed (no sm_103a device?)");
+  if (!stream) {
+    ISG_CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    own_stream = true;
+  }
+  return ISING_OK;
+}
+
+void FilmSet::layout(bool assign_part) {
+  uint32_t ub = 0, mb = 0;
+  size_t po = 0;
+  for (auto& d : h) {
+    d.upd_block_begin = ub;
+    d.meas_block_begin = mb;
+    if (assign_part) d.part_off = po;
+    ub += (d.upd_items + kUpdateBlock - 1) / kUpdateBlock;
+    mb += d.Lx * d.meas_bpl;
+    po += part_len(d);
+  }
+  hh.n_films = (uint32_t)h.size();
+  hh.upd_blocks = ub;
+  hh.meas_blocks = mb;
+}
+
+int FilmSet::upload() {
+  const size_t nf = h.size();
+  const size_t bytes = sizeof(LaunchHdr) + nf * sizeof(FilmDesc) + (hh.upd_blocks + hh.meas_blocks) * sizeof(uint32_t);
+  if (bytes > meta_bytes) {
+    if (d_meta) {
+      ISG_CK(cudaStreamSynchronize(stream));
+      ISG_CK(cudaFree(d_meta));
+      d_meta = nullptr;
+    }
+    const size_t cap = std::max(bytes, meta_bytes * 2);
+    ISG_CK(cudaMalloc(&d_meta, cap));
+    meta_bytes = cap;
+  }
+  staging.resize(bytes);
+  char* p = staging.data();
+  std::memcpy(p, &hh, sizeof hh);
+  std::memcpy(p + sizeof hh, h.data(), nf * sizeof(FilmDesc));
+  uint32_t* ou = reinterpret_cast<uint32_t*>(p + sizeof hh + nf * sizeof(FilmDesc));
+  uint32_t* om = ou + hh.upd_blocks;
+  for (size_t f = 0; f < nf; f++) {
+    const FilmDesc& d = h[f];
+    const uint32_t nb = (d.upd_items + kUpdateBlock - 1) / kUpdateBlock;
+    for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
+    for (uint32_t b = 0; b < d.Lx * d.meas_bpl; b++) om[d.meas_block_begin + b] = (uint32_t)f;
+  }
+  L.hdr = reinterpret_cast<LaunchHdr*>(d_meta);
+  L.films = reinterpret_cast<FilmDesc*>(d_meta + sizeof hh);
+  L.owner_upd = reinterpret_cast<uint32_t*>(d_meta + sizeof hh + nf * sizeof(FilmDesc));
+  L.owner_meas = L.owner_upd + hh.upd_blocks;
+  ISG_CK(cudaMemcpyAsync(d_meta, p, bytes, cudaMemcpyHostToDevice, stream));
+  ISG_CK(cudaStreamSynchronize(stream));
+  return ISING_OK;
+}
+
+uint32_t FilmSet::upd_grid() const { return std::min<uint32_t>(hh.upd_blocks, upd_grid_max()); }
+uint32_t FilmSet::meas_grid() const { return std::min<uint32_t>(hh.meas_blocks, meas_grid_max()); }
+uint32_t FilmSet::fin_grid() const { return std::min<uint32_t>(hh.n_films, (uint32_t)(2 * n_sm)); }
+
+int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_grid) {
+  const uint32_t ug = fixed_grid ? upd_grid_max() : upd_grid();
+  const uint32_t mg = fixed_grid ? meas_grid_max() : meas_grid();
+  const uint32_t fg = fixed_grid ? (uint32_t)(2 * n_sm) : fin_grid();
+  for (uint32_t k = k0; k < k0 + n; k++) {
+    ISG_CK(launch_update(L, ug, pool, 0, k, stream));
+    ISG_CK(launch_update(L, ug, pool, 1, k, stream));
+    bool meas = all_meas;
+    if (!meas)
+      for (const auto& d : h)
+        if (d.active && d.measure_every && (uint64_t)(d.sweep + k + 1) % d.measure_every == 0 &&
+            (uint64_t)d.sweep + k + 1 <= d.sweep_end) {
+          meas = true;
+          break;
+        }
+    if (meas) ISG_CK(launch_measure(L, mg, fg, pool, part, rec, k + 1, 0, nullptr, stream));
+  }
+  return ISING_OK;
+}
+
+int FilmSet::release() {
+  if (stream) cudaStreamSynchronize(stream);
+  if (d_meta) cudaFree(d_meta);
+  if (pool) cudaFree(pool);
+  if (part) cudaFree(part);
+  if (rec) cudaFree(rec);
+  d_meta = nullptr;
+  pool = nullptr;
+  part = nullptr;
+  rec = nullptr;
+  if (own_stream && stream) cudaStreamDestroy(stream);
+  stream = nullptr;
+  own_stream = false;
+  return ISING_OK;
+}
+
+int wait_stream(cudaStream_t st, double timeout_s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return ISING_OK;
+    if (e != cudaErrorNotReady) return fail(ISING_ECUDA, "stream: %s", cudaGetErrorString(e));
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (dt > timeout_s) return fail(ISING_ETIMEOUT, "wait timed out after %.3f s", dt);
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+// ---------------------------------------------------------------- one film
+
+struct ising {
+  FilmSet fs;
+  double J = 1.0, H = 0.0, H1 = 0.0, T = 1.0;
+  uint64_t seed = 0;
+  int y_mode = ISING_Y_GAPBC, x_mode = ISING_X_FREE;
+  uint32_t replica = 0;
+  uint64_t rec_written = 0, rec_read = 0;  // ring counters (mirror of the device's rec_next)
+  int64_t* d_direct = nullptr;
+  int8_t* d_stage = nullptr;
+  bool dirty = true;
+  FilmDesc& d() { return fs.h[0]; }
+};
+
+namespace {
+
+int ensure_stage(ising* h) {
+  if (!h->d_stage) ISG_CK(cudaMalloc(&h->d_stage, (size_t)h->d().Lx * h->d().Ly * h->d().Lz));
+  return ISING_OK;
+}
+
+int sync_desc(ising* h) {
+  if (!h->dirty) return ISING_OK;
+  int rc = h->fs.upload();
+  if (rc) return rc;
+  h->dirty = false;
+  return ISING_OK;
+}
+
+// Grow the record ring so that `extra` more records fit beside the pending ones.
+int ensure_ring(ising* h, uint64_t extra) {
+  FilmDesc& d = h->d();
+  const uint64_t pending = h->rec_written - h->rec_read;
+  if (pending + extra <= d.rec_cap) return ISING_OK;
+  uint64_t cap = std::max<uint64_t>({64, 2 * (uint64_t)d.rec_cap, pending + extra});
+  if (cap > 0xFFFFFFF0ull) return fail(ISING_ENOMEM, "record series too long; read it out first");
+  const size_t rl = record_len(d);
+  int64_t* nr = nullptr;
+  if (cudaMalloc(&nr, cap * rl * sizeof(int64_t)) != cudaSuccess)
+    return fail(ISING_ENOMEM, "cannot allocate %llu records", (unsigned long long)cap);
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  for (uint64_t i = 0; i < pending; i++) {
+    const uint64_t slot = (h->rec_read + i) % d.rec_cap;
+    ISG_CK(cudaMemcpyAsync(nr + i * rl, h->fs.rec + slot * rl, rl * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                           h->fs.stream));
+  }
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  if (h->fs.rec) cudaFree(h->fs.rec);
+  h->fs.rec = nr;
+  h->fs.rec_words = cap * rl;
+  d.rec_off = 0;
+  d.rec_cap = (uint32_t)cap;
+  d.rec_next = (uint32_t)pending;
+  h->rec_read = 0;
+  h->rec_written = pending;
+  h->dirty = true;
+  return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ising_create(int Lx, int Ly, int Lz, double J, double H1, double T, uint64_t seed, ising** out) {
+  clear_error();
+  if (!out) return fail(ISING_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = check_film(Lx, Ly, Lz, T, ISING_Y_GAPBC, ISING_X_FREE);
+  if (rc) return rc;
+  ising* h = new (std::nothrow) ising();
+  if (!h) return fail(ISING_ENOMEM, "host allocation failed");
+  h->J = J;
+  h->H1 = H1;
+  h->T = T;
+  h->seed = seed;
+  h->fs.h.resize(1);
+  FilmDesc& d = h->fs.h[0];
+  std::memset(&d, 0, sizeof d);
+  fill_geometry(d, Lx, Ly, Lz, ISING_Y_GAPBC, ISING_X_FREE, seed, 0);
+  build_tables(d, J, 0.0, H1, T);
+  rc = h->fs.init_device();
+  if (rc) { delete h; return rc; }
+  h->fs.layout();
+  const size_t words = film_words(d);
+  if (cudaMalloc(&h->fs.pool, words * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&h->fs.part, part_len(d) * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&h->d_direct, record_len(d) * sizeof(int64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->d_direct);
+    delete h;
+    return fail(ISING_ENOMEM, "device allocation failed");
+  }
+  h->fs.pool_words = words;
+  rc = ensure_ring(h, 64);
+  if (!rc) rc = launch_init(d, h->fs.pool, ISING_INIT_ALL_UP, 0, 0, h->fs.stream) == cudaSuccess ? ISING_OK
+                                                                                           : fail(ISING_ECUDA, "init launch failed");
+  if (!rc) rc = sync_desc(h);
+  if (rc) { ising_destroy(h); return rc; }
+  *out = h;
+  return ISING_OK;
+}
+
+int ising_set_options(ising* h, int y_mode, int x_mode, double H, uint32_t replica) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  FilmDesc& d = h->d();
+  int rc = check_film((int)d.Lx, (int)d.Ly, (int)d.Lz, h->T, y_mode, x_mode);
+  if (rc) return rc;
+  h->y_mode = y_mode;
+  h->x_mode = x_mode;
+  h->H = H;
+  h->replica = replica;
+  d.y_mode = (uint32_t)y_mode;
+  d.x_pbc = x_mode == ISING_X_PBC;
+  d.key1 = replica;
+  build_tables(d, h->J, H, h->H1, h->T);
+  h->dirty = true;
+  return ISING_OK;
+}
+
+int ising_set_params(ising* h, double J, double H1, double T) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  if (!(T > 0.0)) return fail(ISING_EINVAL, "T must be > 0");
+  h->J = J;
+  h->H1 = H1;
+  h->T = T;
+  build_tables(h->d(), J, h->H, H1, T);
+  h->dirty = true;
+  return ISING_OK;
+}
+
+int ising_set_stream(ising* h, void* s) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  if (h->fs.own_stream) ISG_CK(cudaStreamDestroy(h->fs.stream));
+  h->fs.own_stream = false;
+  h->fs.stream = nullptr;
+  if (s) {
+    h->fs.stream = (cudaStream_t)s;
+  } else {
+    ISG_CK(cudaStreamCreateWithFlags(&h->fs.stream, cudaStreamNonBlocking));
+    h->fs.own_stream = true;
+  }
+  return ISING_OK;
+}
+
+int ising_init(ising* h, int kind, double flip_p) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  if (kind < ISING_INIT_RANDOM || kind > ISING_INIT_ALL_UP) return fail(ISING_EINVAL, "bad init kind %d", kind);
+  uint32_t flip_lo = 0;
+  int flip_all = 0;
+  if (kind == ISING_INIT_SLAB_Y) {
+    if (!(flip_p >= 0.0 && flip_p <= 1.0)) return fail(ISING_EINVAL, "flip_p must be in [0,1]");
+    const double t = std::floor(std::ldexp(flip_p, 32));
+    if (t >= 4294967296.0) flip_all = 1; else flip_lo = (uint32_t)t;
+  }
+  FilmDesc& d = h->d();
+  ISG_CK(launch_init(d, h->fs.pool, kind, flip_lo, flip_all, h->fs.stream));
+  d.sweep = 0;
+  d.rec_next = 0;
+  h->rec_written = h->rec_read = 0;
+  h->dirty = true;
+  return sync_desc(h);
+}
+
+int ising_set_spins(ising* h, const int8_t* s) {
+  clear_error();
+  if (!h || !s) return fail(ISING_EINVAL, "NULL argument");
+  int rc = ensure_stage(h);
+  if (rc) return rc;
+  const FilmDesc& d = h->d();
+  ISG_CK(cudaMemcpyAsync(h->d_stage, s, (size_t)d.Lx * d.Ly * d.Lz, cudaMemcpyHostToDevice, h->fs.stream));
+  ISG_CK(launch_pack(d, h->fs.pool, h->d_stage, h->fs.stream));
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  return ISING_OK;
+}
+
+int ising_get_spins(ising* h, int8_t* s) {
+  clear_error();
+  if (!h || !s) return fail(ISING_EINVAL, "NULL argument");
+  int rc = ensure_stage(h);
+  if (rc) return rc;
+  const FilmDesc& d = h->d();
+  ISG_CK(launch_unpack(d, h->fs.pool, h->d_stage, h->fs.stream));
+  ISG_CK(cudaMemcpyAsync(s, h->d_stage, (size_t)d.Lx * d.Ly * d.Lz, cudaMemcpyDeviceToHost, h->fs.stream));
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  return ISING_OK;
+}
+
+int ising_set_spins_device(ising* h, const int8_t* s) {
+  clear_error();
+  if (!h || !s) return fail(ISING_EINVAL, "NULL argument");
+  ISG_CK(launch_pack(h->d(), h->fs.pool, s, h->fs.stream));
+  return ISING_OK;
+}
+
+int ising_get_spins_device(ising* h, int8_t* s) {
+  clear_error();
+  if (!h || !s) return fail(ISING_EINVAL, "NULL argument");
+  ISG_CK(launch_unpack(h->d(), h->fs.pool, s, h->fs.stream));
+  return ISING_OK;
+}
+
+size_t ising_packed_words(const ising* h) { return h ? film_words(const_cast<ising*>(h)->d()) : 0; }
+
+int ising_get_packed_device(ising* h, uint32_t* dst) {
+  clear_error();
+  if (!h || !dst) return fail(ISING_EINVAL, "NULL argument");
+  ISG_CK(cudaMemcpyAsync(dst, h->fs.pool, film_words(h->d()) * 4, cudaMemcpyDeviceToDevice, h->fs.stream));
+  return ISING_OK;
+}
+
+int ising_set_packed_device(ising* h, const uint32_t* src) {
+  clear_error();
+  if (!h || !src) return fail(ISING_EINVAL, "NULL argument");
+  ISG_CK(cudaMemcpyAsync(h->fs.pool, src, film_words(h->d()) * 4, cudaMemcpyDeviceToDevice, h->fs.stream));
+  return ISING_OK;
+}
+
+int ising_get_sweep(const ising* h, uint64_t* sweep) {
+  clear_error();
+  if (!h || !sweep) return fail(ISING_EINVAL, "NULL argument");
+  *sweep = const_cast<ising*>(h)->d().sweep;
+  return ISING_OK;
+}
+
+int ising_set_sweep(ising* h, uint64_t sweep) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  if (sweep >= 0xFFFFFFFFull) return fail(ISING_EINVAL, "sweep index must stay below 0xFFFFFFFF");
+  h->d().sweep = (uint32_t)sweep;
+  h->dirty = true;
+  return sync_desc(h);
+}
+
+int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  FilmDesc& d = h->d();
+  if (n == 0) return ISING_OK;
+  if ((uint64_t)d.sweep + n >= 0xFFFFFFFFull) return fail(ISING_EINVAL, "sweep counter would reach 0xFFFFFFFF");
+  if (d.measure_every != measure_every) {
+    d.measure_every = measure_every;
+    h->dirty = true;
+  }
+  const uint64_t s0 = d.sweep;
+  const uint64_t nrec = measure_every ? (s0 + n) / measure_every - s0 / measure_every : 0;
+  int rc = ensure_ring(h, nrec);
+  if (rc) return rc;
+  rc = sync_desc(h);
+  if (rc) return rc;
+  rc = h->fs.enqueue_sweeps(0, (uint32_t)n, false, false);
+  if (rc) return rc;
+  ISG_CK(launch_advance(h->fs.L, 1, (uint32_t)n, h->fs.stream));
+  d.sweep = (uint32_t)(s0 + n);
+  d.rec_next += (uint32_t)nrec;
+  h->rec_written += nrec;
+  return ISING_OK;
+}
+
+int ising_measure(ising* h, ising_obs* out) {
+  clear_error();
+  if (!h || !out) return fail(ISING_EINVAL, "NULL argument");
+  int rc = sync_desc(h);
+  if (rc) return rc;
+  FilmDesc& d = h->d();
+  ISG_CK(launch_measure(h->fs.L, h->fs.meas_grid(), 1, h->fs.pool, h->fs.part, h->fs.rec, 0, 1, h->d_direct,
+                        h->fs.stream));
+  std::vector<int64_t> r(record_len(d));
+  ISG_CK(cudaMemcpyAsync(r.data(), h->d_direct, r.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, h->fs.stream));
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  out->sweep = (uint64_t)r[0];
+  out->bond_sum = r[1];
+  out->M = r[2];
+  out->M1 = r[3];
+  out->Mn = r[4];
+  if (out->m_x) std::memcpy(out->m_x, r.data() + 5, d.Lx * sizeof(int64_t));
+  return ISING_OK;
+}
+
+int ising_read_series(ising* h, int64_t* buf, size_t cap, size_t* n_records) {
+  clear_error();
+  if (!h || !n_records || (cap && !buf)) return fail(ISING_EINVAL, "NULL argument");
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  const FilmDesc& d = h->d();
+  const size_t rl = record_len(d);
+  const uint64_t pending = h->rec_written - h->rec_read;
+  const uint64_t k = std::min<uint64_t>(pending, cap);
+  uint64_t i = 0;
+  while (i < k) {
+    const uint64_t slot = (h->rec_read + i) % d.rec_cap;
+    const uint64_t run = std::min<uint64_t>(k - i, d.rec_cap - slot);
+    ISG_CK(cudaMemcpyAsync(buf + i * rl, h->fs.rec + d.rec_off + slot * rl, run * rl * sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, h->fs.stream));
+    i += run;
+  }
+  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  h->rec_read += k;
+  *n_records = (size_t)k;
+  return ISING_OK;
+}
+
+int ising_pending_records(const ising* h, size_t* n) {
+  clear_error();
+  if (!h || !n) return fail(ISING_EINVAL, "NULL argument");
+  *n = (size_t)(h->rec_written - h->rec_read);
+  return ISING_OK;
+}
+
+int ising_synchronize(ising* h, double timeout_s) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  return wait_stream(h->fs.stream, timeout_s);
+}
+
+int ising_destroy(ising* h) {
+  if (!h) return ISING_OK;
+  h->fs.release();
+  if (h->d_direct) cudaFree(h->d_direct);
+  if (h->d_stage) cudaFree(h->d_stage);
+  delete h;
+  return ISING_OK;
+}
+
+const char* ising_strerror(int status) {
+  switch (status) {
+    case ISING_OK: return "ok";
+    case ISING_EINVAL: return "invalid argument";
+    case ISING_ENOMEM: return "out of memory";
+    case ISING_ECUDA: return "CUDA error";
+    case ISING_ETIMEOUT: return "timed out";
+    case ISING_EBUSY: return "busy";
+    case ISING_ENOTFOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+const char* ising_last_error(void) { return last_error(); }
+
+int ising_version(int* major, int* minor, int* sm) {
+  if (major) *major = 0;
+  if (minor) *minor = 1;
+  if (sm) *sm = 103;
+  return ISING_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Device-side definitions shared by the Ising-film kernels (sm_103a).
+//
+// Lattice store.  A film Lx x Ly x Lz has Lx*Ly rows (kx,ky), row index
+// (kx-1)*Ly + (ky-1).  Each row is split by the parity X = z0 & 1 of
+// z0 = kz-1 into two arrays of n = Lz/2 sites, site j of array X being
+// z0 = 2j + X.  An array is W = ceil(n/32) 32-bit words; the film's words are
+// laid out [X][row][w] (one "plane" per parity, rows contiguous, z fastest).
+// Inside a word, local site l (0..31) sits at bit (l >> 2) + 8*(l & 3), so the
+// four sites l = 4q..4q+3 served by one Philox call occupy bit q of each of
+// the four bytes.  Bit = 1 means S = +1.  Padding bits (j >= n) stay 0.
+//
+// Checkerboard (Appendix) with colour c = (kx+ky+kz) mod 2: in half-sweep c a
+// row (kx,ky) updates array X = (kx + ky + 1 + c) & 1 and reads the same array
+// of its x/y neighbour rows (which update the other array) and both
+// z-neighbours from its own other array.
+#pragma once
+#include <cstdint>
+
+namespace isg {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kWeyl0 = 0x9E3779B9u;
+constexpr uint32_t kWeyl1 = 0xBB67AE85u;
+constexpr uint32_t kInitSweep = 0xFFFFFFFFu;
+
+enum : uint32_t { kYGapbc = 0, kYPbc = 1, kYApbc = 2 };
+
+// One film of a launch.  Lives in device memory; counters `sweep` and
+// `rec_next` are advanced by kernels so that captured graphs can be replayed.
+struct FilmDesc {
+  uint32_t Lx, Ly, Lz, n, W;   // n = Lz/2 sites per array, W words per array
+  uint32_t y_mode, x_pbc;
+  uint32_t key0, key1;         // Philox key
+  uint32_t last_mask;          // valid bits of word W-1
+  uint32_t last_calls;         // Philox calls needed by word W-1 (1..8)
+  uint32_t upd_block_begin;    // first block of this film in the update grid
+  uint32_t upd_items;          // Lx*(Ly-1)*W
+  uint32_t meas_block_begin;   // first block in the measurement grid
+  uint32_t meas_bpl;           // measurement blocks per layer
+  uint32_t measure_every;      // 0 = never
+  uint32_t sweep;              // absolute index of chunk sweep 0
+  uint32_t sweep_end;          // the film stops before this sweep index
+  uint32_t rec_next;           // records written so far
+  uint32_t rec_cap;            // ring capacity (records)
+  uint32_t active;             // 0 = skip this film
+  uint64_t spin_off;           // word offset of plane X=0 in the spin pool
+  uint64_t rec_off;            // int64 offset of the record ring
+  uint64_t part_off;           // int64 offset of this film's partial sums
+  uint32_t thr[4][16];         // Metropolis thresholds [class][s + 2*n_aligned]
+  uint32_t always[4];          // bit (s + 2*n_aligned): accept without a draw
+};
+
+// Work sizes of a launch, read by the kernels from device memory so that a
+// captured chunk can be replayed while films come and go.
+struct LaunchHdr {
+  uint32_t n_films;
+  uint32_t upd_blocks;   // virtual update blocks (owner table length)
+  uint32_t meas_blocks;  // virtual measurement blocks
+  uint32_t pad;
+};
+
+// Row class of layer kx: 0 bulk, 1 first layer, 2 last layer, 3 both (Lx=1).
+__host__ __device__ inline uint32_t row_class(uint32_t kx, uint32_t Lx) {
+  return (kx == 1 ? 1u : 0u) | (kx == Lx ? 2u : 0u);
+}
+
+// Bit position of local site l inside its word.
+__host__ __device__ inline uint32_t bitpos(uint32_t l) { return (l >> 2) + 8u * (l & 3u); }
+
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t mulhi(uint32_t a, uint32_t b) { return __umulhi(a, b); }
+
+// Philox4x32-10 (Salmon et al., SC'11) for counter (c0,c1,c2,c3), key (k0,k1).
+__device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                         uint32_t k0, uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    uint32_t lo0 = kPhiloxM0 * c0, hi0 = mulhi(kPhiloxM0, c0);
+    uint32_t lo1 = kPhiloxM1 * c2, hi1 = mulhi(kPhiloxM1, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += kWeyl0;
+    k1 += kWeyl1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Philox calls that share the row, sweep and parity words of the counter:
+// the first round and half of the second depend only on those, so they are
+// computed once per row and reused for the eight calls of a word.
+struct PhiloxRow {
+  uint32_t r1_hi1, r1_c3, r2_c0, r2_c1;
+  uint32_t r1_x2;
+  uint32_t k0, k1;
+  __device__ __forceinline__ PhiloxRow(uint32_t row, uint32_t sweep, uint32_t parity, uint32_t key0,
+                                       uint32_t key1) {
+    k0 = key0;
+    k1 = key1;
+    // round 1 with counter (row, c1, sweep, parity): words 1..3 of the result
+    // do not depend on c1.
+    uint32_t lo0 = kPhiloxM0 * row, hi0 = mulhi(kPhiloxM0, row);
+    uint32_t lo1 = kPhiloxM1 * sweep, hi1 = mulhi(kPhiloxM1, sweep);
+    r1_hi1 = hi1;            // x0 = hi1 ^ c1 ^ k0
+    uint32_t x1 = lo1;
+    r1_x2 = hi0 ^ parity ^ key1;
+    r1_c3 = lo0;
+    // round 2: the products of x2 are c1-independent
+    uint32_t k0b = key0 + kWeyl0;
+    uint32_t lo1b = kPhiloxM1 * r1_x2, hi1b = mulhi(kPhiloxM1, r1_x2);
+    r2_c0 = hi1b ^ x1 ^ k0b;
+    r2_c1 = lo1b;
+  }
+  // Full Philox4x32-10 output for counter word 1 = c1.
+  __device__ __forceinline__ void draw(uint32_t c1, uint32_t out[4]) const {
+    uint32_t x0 = r1_hi1 ^ c1 ^ k0;  // end of round 1 (x1 = lo1, x2 = r1_x2, x3 = r1_c3)
+    uint32_t k1b = k1 + kWeyl1;
+    uint32_t lo0 = kPhiloxM0 * x0, hi0 = mulhi(kPhiloxM0, x0);
+    uint32_t c0 = r2_c0, c1w = r2_c1, c2 = hi0 ^ r1_c3 ^ k1b, c3 = lo0;  // end of round 2
+    uint32_t kk0 = k0 + 2u * kWeyl0, kk1 = k1 + 2u * kWeyl1;
+#pragma unroll
+    for (int r = 2; r < 10; r++) {
+      uint32_t l0 = kPhiloxM0 * c0, h0 = mulhi(kPhiloxM0, c0);
+      uint32_t l1 = kPhiloxM1 * c2, h1 = mulhi(kPhiloxM1, c2);
+      c0 = h1 ^ c1w ^ kk0;
+      c1w = l1;
+      c2 = h0 ^ c3 ^ kk1;
+      c3 = l0;
+      kk0 += kWeyl0;
+      kk1 += kWeyl1;
+    }
+    out[0] = c0; out[1] = c1w; out[2] = c2; out[3] = c3;
+  }
+};
+
+// Word whose local site l holds site l-1 of the array (z-1 neighbour of
+// parity-0 sites), `prev` being the word before (its bit 31 = local site 31).
+__device__ __forceinline__ uint32_t shift_prev(uint32_t v, uint32_t prev) {
+  return (v << 8) | ((v >> 23) & 0xFEu) | (prev >> 31);
+}
+// Word whose local site l holds site l+1 (z+1 neighbour of parity-1 sites).
+__device__ __forceinline__ uint32_t shift_next(uint32_t v, uint32_t next) {
+  return (v >> 8) | ((v << 23) & 0x7F000000u) | (next << 31);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace isg

@@ -1,0 +1,81 @@
+// Host-side internals shared by the API translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ising.h"
+#include "ising_device.cuh"
+#include "ising_launch.h"
+
+namespace isg {
+
+int fail(int code, const char* fmt, ...);
+void clear_error();
+const char* last_error();
+
+// Polls a stream until it is idle or timeout_s passes (ETIMEOUT).
+int wait_stream(cudaStream_t st, double timeout_s);
+
+#define ISG_CK(call)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return ::isg::fail(ISING_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Validates a film's sizes and parameters; EINVAL with a message otherwise.
+int check_film(int Lx, int Ly, int Lz, double T, int y_mode, int x_mode);
+
+// Geometry, key and work sizes of a descriptor (no offsets, no tables).
+void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, uint64_t seed, uint32_t replica);
+
+// Metropolis thresholds of Eq. 1 for the four row classes (binary64, libm exp).
+void build_tables(FilmDesc& d, double J, double H, double H1, double T);
+
+// Packed words of one film (both parity planes).
+inline size_t film_words(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.Ly * d.W; }
+inline size_t record_len(const FilmDesc& d) { return 5 + (size_t)d.Lx; }
+inline size_t part_len(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.meas_bpl; }
+
+// Films updated by the same launches: descriptors, owner tables and the
+// device buffers they point into.
+struct FilmSet {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n_sm = 0, upd_per_sm = 0, meas_per_sm = 0;
+
+  std::vector<FilmDesc> h;  // host mirror (counters tracked on the host too)
+  LaunchHdr hh{};
+  LaunchSet L;
+  char* d_meta = nullptr;   // [hdr | films | owner_upd | owner_meas]
+  size_t meta_bytes = 0;
+  std::vector<char> staging;
+
+  uint32_t* pool = nullptr;
+  size_t pool_words = 0;
+  int64_t* part = nullptr;
+  size_t part_words = 0;
+  int64_t* rec = nullptr;
+  size_t rec_words = 0;
+
+  int init_device();          // device, stream, occupancy
+  void layout(bool assign_part = true);  // block ranges, owner tables, partial offsets
+  int upload();               // copies hdr/films/owners to the device (synchronous)
+  uint32_t upd_grid() const;  // grid of a direct launch
+  uint32_t meas_grid() const;
+  uint32_t fin_grid() const;
+  uint32_t upd_grid_max() const { return (uint32_t)(n_sm * upd_per_sm); }
+  uint32_t meas_grid_max() const { return (uint32_t)(n_sm * meas_per_sm); }
+  // Kernels of sweeps k0..k0+n-1 of the current chunk, with measurements
+  // where some film's measure_every divides (sweep + k + 1) (all_meas: after
+  // every sweep, films decide on the device).
+  int enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_grid);
+  int release();
+  ~FilmSet() { release(); }
+};
+
+}  // namespace isg

@@ -1,0 +1,188 @@
+"""GPU path vs the CPU oracle, bit for bit (spins and int64 records).
+
+Every case runs the same seeded chain on both sides -- same counter-based
+Philox stream, same four-phase schedule, same binary64 thresholds -- so the
+spin configuration and every record must be identical after any number of
+sweeps.  Shapes cover several words per row with a ragged last word, a
+single partial word, Lz = 2 (double z bonds), Ly = 2, Lx = 1, odd and even
+Lx + Ly (the Eq. 11 wrap joining equal or opposite colours), periodic x, and
+the degenerate temperatures beta = 0 and T -> 0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1411_5588_gb300 as ig
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+#        Lx  Ly  Lz   y_mode      x_mode    H1     H    T      init            flip
+CASES = [
+    (8, 8, 8, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 3.0, ig.INIT_RANDOM, 0.0),
+    (5, 6, 66, ig.Y_GAPBC, ig.X_FREE, 0.55, 0.0, 2.5, ig.INIT_RANDOM, 0.0),
+    (3, 4, 2, ig.Y_GAPBC, ig.X_FREE, 0.3, 0.0, 2.0, ig.INIT_RANDOM, 0.0),
+    (1, 8, 16, ig.Y_GAPBC, ig.X_FREE, 0.7, 0.0, 2.2, ig.INIT_RANDOM, 0.0),
+    (4, 3, 130, ig.Y_PBC, ig.X_FREE, 0.2, 0.0, 3.5, ig.INIT_RANDOM, 0.0),
+    (6, 2, 64, ig.Y_APBC, ig.X_FREE, 0.4, 0.0, 3.0, ig.INIT_RANDOM, 0.0),
+    (7, 5, 128, ig.Y_GAPBC, ig.X_FREE, 0.45, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01),
+    (6, 5, 200, ig.Y_GAPBC, ig.X_FREE, 0.45, 0.0, 2.0, ig.INIT_SLAB_Y, 0.05),
+    (4, 4, 8, ig.Y_PBC, ig.X_PBC, 0.0, 0.0, 4.5, ig.INIT_RANDOM, 0.0),
+    (9, 10, 190, ig.Y_GAPBC, ig.X_FREE, -0.3, 0.1, 1.5, ig.INIT_SLAB_Y, 0.01),
+    (5, 7, 64, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, math.inf, ig.INIT_RANDOM, 0.0),
+    (5, 7, 64, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 1e-3, ig.INIT_RANDOM, 0.0),
+    (3, 3, 6, ig.Y_GAPBC, ig.X_FREE, 1.0, 0.0, 1.5, ig.INIT_ALL_UP, 0.0),
+    (2, 9, 34, ig.Y_APBC, ig.X_PBC, 0.25, -0.2, 2.8, ig.INIT_RANDOM, 0.0),
+    (16, 12, 96, ig.Y_GAPBC, ig.X_FREE, 0.55, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01),
+]
+
+
+def _pair(case, seed=7, replica=3):
+    Lx, Ly, Lz, ym, xm, H1, H, T, kind, flip = case
+    g = ig.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica)
+    o = O.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica)
+    g.init(kind, flip)
+    o.init(kind, flip)
+    return g, o
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-y{c[3]}x{c[4]}-T{c[7]}" for c in CASES])
+def test_sweeps_bit_exact(case):
+    g, o = _pair(case)
+    assert np.array_equal(g.get_spins(), o.get_spins()), "initial state differs"
+    done = 0
+    for n, m in ((1, 1), (1, 1), (8, 2), (90, 3)):
+        g.sweep(n, m)
+        want = o.sweep(n, m)
+        got = g.read_series()
+        done += n
+        assert g.sweep_count == done
+        assert np.array_equal(got, want), f"records differ after {done} sweeps"
+        assert np.array_equal(g.get_spins(), o.get_spins()), f"spins differ after {done} sweeps"
+    assert np.array_equal(g.measure(), o.measure())
+    g.close()
+
+
+def test_measure_matches_oracle_on_given_spins():
+    rng = np.random.default_rng(5)
+    for Lx, Ly, Lz, ym in [(5, 6, 66, ig.Y_GAPBC), (3, 4, 2, ig.Y_APBC), (6, 5, 200, ig.Y_PBC)]:
+        s = np.where(rng.random(Lx * Ly * Lz) < 0.5, 1, -1).astype(np.int8)
+        g = ig.Film(Lx, Ly, Lz, 1.0, 0.3, 2.0, 1, y_mode=ym)
+        o = O.Film(Lx, Ly, Lz, 1.0, 0.3, 2.0, 1, y_mode=ym)
+        g.set_spins(s)
+        o.set_spins(s)
+        assert np.array_equal(g.get_spins(), s)
+        assert np.array_equal(g.measure(), o.measure())
+        g.close()
+
+
+def test_checkpoint_resume_is_bit_exact():
+    case = (7, 6, 70, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 2.6, ig.INIT_RANDOM, 0.0)
+    g, o = _pair(case, seed=11)
+    g.sweep(37, 0)
+    saved, at = g.get_spins(), g.sweep_count
+    g.close()
+    h = ig.Film(7, 6, 70, 1.0, 0.5, 2.6, 11, replica=3)
+    h.set_spins(saved)
+    h.sweep_count = at
+    h.sweep(63, 7)
+    rec = h.read_series()
+    o.sweep(37, 0)
+    want = o.sweep(63, 7)
+    assert np.array_equal(rec, want)
+    assert np.array_equal(h.get_spins(), o.get_spins())
+    h.close()
+
+
+def test_record_ring_grows_and_drains_in_order():
+    case = (4, 5, 40, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 3.0, ig.INIT_RANDOM, 0.0)
+    g, o = _pair(case)
+    g.sweep(150, 1)  # more than the initial ring
+    first = g.read_series(cap=40)
+    g.sweep(200, 1)
+    rest = g.read_series()
+    want = o.sweep(350, 1)
+    assert np.array_equal(np.concatenate([first, rest]), want)
+    g.close()
+
+
+def test_parameter_change_between_sweeps():
+    case = (6, 6, 64, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 3.0, ig.INIT_RANDOM, 0.0)
+    g, o = _pair(case)
+    g.sweep(10, 5)
+    o.sweep(10, 5)
+    g.set_params(1.0, 0.2, 2.2)
+    o2 = O.Film(6, 6, 64, 1.0, 0.2, 2.2, 7, replica=3)
+    o2.set_spins(o.get_spins())
+    o2.sweep_count = o.sweep_count
+    g.sweep(10, 5)
+    want = o2.sweep(10, 5)
+    got = g.read_series()
+    assert np.array_equal(got[2:], want)
+    assert np.array_equal(g.get_spins(), o2.get_spins())
+    g.close()
+
+
+def test_paper_scale_film_bit_exact():
+    """The 120 x 240 x 1600 film (46,080,000 spins), slab start with 1% flips,
+    +H1 = 0.55 at T = 3, in the launch configuration the benchmark times
+    (records every 10 sweeps)."""
+    Lx, Ly, Lz = 120, 240, 1600
+    g = ig.Film(Lx, Ly, Lz, 1.0, 0.55, 3.0, 2)
+    o = O.Film(Lx, Ly, Lz, 1.0, 0.55, 3.0, 2)
+    g.init(ig.INIT_SLAB_Y, 0.01)
+    o.init(O.INIT_SLAB_Y, 0.01)
+    g.sweep(20, 10)
+    want = o.sweep(20, 10)
+    assert np.array_equal(g.read_series(), want)
+    assert np.array_equal(g.get_spins(), o.get_spins())
+    g.close()
+
+
+def test_mixed_batch_matches_films_run_alone():
+    specs = []
+    for i, (Lx, Ly, Lz) in enumerate([(8, 8, 8), (5, 6, 66), (3, 4, 2), (7, 5, 128), (1, 8, 16), (16, 12, 96)]):
+        specs.append(dict(Lx=Lx, Ly=Ly, Lz=Lz, T=2.0 + 0.3 * i, H1=0.1 * i, seed=100 + i, replica=i,
+                          measure_every=(i % 3) + 1, init_kind=ig.INIT_RANDOM if i % 2 else ig.INIT_SLAB_Y,
+                          flip_p=0.02, y_mode=[ig.Y_GAPBC, ig.Y_PBC, ig.Y_APBC][i % 3]))
+    for use_graph in (False, True):
+        b = ig.Batch(specs)
+        b.sweep(5, use_graph)
+        b.sweep(91, use_graph)
+        for i, sp in enumerate(specs):
+            o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], y_mode=sp["y_mode"],
+                       replica=sp["replica"])
+            o.init(sp["init_kind"], sp["flip_p"])
+            want = o.sweep(96, sp["measure_every"])
+            assert np.array_equal(b.read_series(i), want), (use_graph, i)
+            assert np.array_equal(b.get_spins(i), o.get_spins()), (use_graph, i)
+        b.close()
+
+
+def test_thermodynamic_integration_from_gpu_records_matches_oracle():
+    """Eq. 9 over 8 Gauss-Legendre nodes in H1: the FP64 result from the GPU's
+    records through the library equals the oracle-fed numpy result to 1e-12."""
+    from oracle import ti as OT
+    H1max, n = 0.6, 8
+    xs, _ = ig.gauss_legendre(n, 0.0, H1max)
+    specs = [dict(Lx=6, Ly=8, Lz=16, T=3.0, H1=float(h), seed=5, replica=r, measure_every=1, y_mode=ig.Y_PBC,
+                  init_kind=ig.INIT_ALL_UP) for r, h in enumerate(xs)]
+    b = ig.Batch(specs)
+    b.sweep(300, True)
+    m1g, mng, m1o, mno = [], [], [], []
+    area = 8 * 16
+    for i, sp in enumerate(specs):
+        r = b.read_series(i)
+        o = O.Film(6, 8, 16, 1.0, sp["H1"], 3.0, 5, y_mode=O.Y_PBC, replica=i)
+        o.init(O.INIT_ALL_UP)
+        ro = o.sweep(300, 1)
+        assert np.array_equal(r, ro)
+        m1g.append(ig.series_mean(r, 3, first=50) / area)
+        mng.append(ig.series_mean(r, 4, first=50) / area)
+        m1o.append(OT.series_mean(ro, 3, first=50) / area)
+        mno.append(OT.series_mean(ro, 4, first=50) / area)
+    a = ig.ti_surface_field(H1max, m1g, mng)
+    c = OT.surface_field_ti(H1max, m1o, mno)
+    assert abs(a - c) <= 1e-12 * abs(c)
+    b.close()

@@ -1,0 +1,66 @@
+"""Continuous-batching server: every job's records and final spins equal the
+oracle's chain for that job alone, whatever else shares the device; the
+arena budget forces queueing; waits are bounded."""
+import numpy as np
+import pytest
+
+import paper_1411_5588_gb300 as ig
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _specs():
+    shapes = [(8, 8, 8), (6, 10, 34), (16, 16, 16), (4, 6, 130), (12, 5, 64), (3, 3, 2), (10, 20, 40),
+              (7, 7, 70), (5, 9, 96), (16, 8, 32), (2, 4, 256), (9, 6, 12)]
+    out = []
+    for i, (Lx, Ly, Lz) in enumerate(shapes):
+        out.append(dict(Lx=Lx, Ly=Ly, Lz=Lz, T=1.5 + 0.25 * i, H1=0.08 * i, seed=3, replica=i,
+                        measure_every=(i % 4) + 1, n_sweeps=37 + 13 * i,
+                        init_kind=[ig.INIT_RANDOM, ig.INIT_SLAB_Y, ig.INIT_ALL_UP][i % 3], flip_p=0.01,
+                        y_mode=[ig.Y_GAPBC, ig.Y_PBC, ig.Y_APBC][i % 3]))
+    return out
+
+
+def _oracle(sp):
+    o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], y_mode=sp["y_mode"],
+               replica=sp["replica"])
+    o.init(sp["init_kind"], sp["flip_p"])
+    recs = o.sweep(sp["n_sweeps"], sp["measure_every"])
+    return recs, o.get_spins()
+
+
+@pytest.mark.parametrize("budget,chunk", [(64 << 20, 16), (1 << 20, 7)])
+def test_server_jobs_match_oracle(budget, chunk):
+    specs = _specs()
+    srv = ig.Server(budget, chunk_sweeps=chunk)
+    tickets = srv.submit(specs[:5])
+    tickets += srv.submit(specs[5:])
+    for t, sp in zip(tickets, specs):
+        srv.wait(t, 300.0)
+        recs, spins, info = srv.result(t)
+        want_r, want_s = _oracle(sp)
+        assert np.array_equal(recs, want_r), t
+        assert np.array_equal(spins, want_s), t
+        assert info["t_submit"] <= info["t_admit"] <= info["t_finish"]
+    st = srv.stats()
+    assert st["finished"] == len(specs) and st["running"] == 0 and st["queued"] == 0
+    assert st["bytes_in_use"] == 0
+    srv.close()
+
+
+def test_server_wait_times_out_and_rejects_oversize():
+    srv = ig.Server(1 << 20, chunk_sweeps=50)
+    with pytest.raises(ig.IsingError) as e:
+        srv.submit([dict(Lx=128, Ly=128, Lz=128, T=3.0, n_sweeps=10)])  # staging alone exceeds 1 MiB
+    assert e.value.status == ig.EINVAL
+    (t,) = srv.submit([dict(Lx=16, Ly=16, Lz=32, T=3.0, n_sweeps=20000, measure_every=0)])
+    with pytest.raises(ig.IsingError) as e:
+        srv.wait(t, 0.0)
+    assert e.value.status == ig.ETIMEOUT
+    with pytest.raises(ig.IsingError) as e:
+        srv.result(t)
+    assert e.value.status == ig.EBUSY
+    srv.wait(t, 300.0)
+    srv.result(t, want_spins=False)
+    srv.close()
