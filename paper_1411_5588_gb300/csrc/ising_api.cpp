@@ -43,8 +43,8 @@ int check_film(int Lx, int Ly, int Lz, double T, int y_mode, int x_mode) {
   if (y_mode < ISING_Y_GAPBC || y_mode > ISING_Y_APBC) return fail(ISING_EINVAL, "bad y_mode %d", y_mode);
   if (x_mode != ISING_X_FREE && x_mode != ISING_X_PBC) return fail(ISING_EINVAL, "bad x_mode %d", x_mode);
   if (x_mode == ISING_X_PBC && (Lx < 2 || (Lx & 1))) return fail(ISING_EINVAL, "periodic x needs even Lx >= 2");
-  const double words = 2.0 * Lx * (double)Ly * ((Lz / 2 + 31) / 32);
-  if ((double)Lx * Ly > 4.0e9 || words > 8.0e9) return fail(ISING_EINVAL, "film too large");
+  const double plane = (double)Lx * (double)Ly * (((Lz / 2 + 31) / 32 + 3) / 4 * 4);
+  if (plane >= 2147483648.0) return fail(ISING_EINVAL, "film too large (2^31 words per parity plane at most)");
   return ISING_OK;
 }
 
@@ -54,6 +54,8 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   d.Lz = (uint32_t)Lz;
   d.n = (uint32_t)Lz / 2;
   d.W = (d.n + 31) / 32;
+  d.Wp = (d.W + 3) / 4 * 4;
+  d.nq = d.Wp / 4;
   const uint32_t r = d.n - 32 * (d.W - 1);  // valid sites of the last word, 1..32
   uint32_t mask = 0;
   for (uint32_t l = 0; l < r; l++) mask |= 1u << bitpos(l);
@@ -67,6 +69,8 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   d.meas_bpl = std::max<uint32_t>(1, (d.Ly * d.W + kMeasureItemsPerBlock - 1) / kMeasureItemsPerBlock);
   d.active = 1;
   d.sweep_end = 0xFFFFFFFFu;
+  fastdiv_magic(d.W, &d.divw_m, &d.divw_l);
+  fastdiv_magic(d.Ly - 1, &d.divy_m, &d.divy_l);
 }
 
 void build_tables(FilmDesc& d, double J, double H, double H1, double T) {
@@ -478,8 +482,15 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
   if (rc) return rc;
   rc = sync_desc(h);
   if (rc) return rc;
-  rc = h->fs.enqueue_sweeps(0, (uint32_t)n, false, false);
-  if (rc) return rc;
+  // single film: the descriptor travels as a kernel parameter
+  for (uint64_t k = 0; k < n; k++) {
+    const uint32_t t = (uint32_t)(s0 + k);
+    ISG_CK(launch_update_film(d, h->fs.pool, 0, t, h->fs.stream));
+    ISG_CK(launch_update_film(d, h->fs.pool, 1, t, h->fs.stream));
+    if (measure_every && (s0 + k + 1) % measure_every == 0)
+      ISG_CK(launch_measure(h->fs.L, h->fs.meas_grid(), 1, h->fs.pool, h->fs.part, h->fs.rec, (uint32_t)(k + 1), 0,
+                            nullptr, h->fs.stream));
+  }
   ISG_CK(launch_advance(h->fs.L, 1, (uint32_t)n, h->fs.stream));
   d.sweep = (uint32_t)(s0 + n);
   d.rec_next += (uint32_t)nrec;

@@ -3,8 +3,11 @@
 // Lattice store.  A film Lx x Ly x Lz has Lx*Ly rows (kx,ky), row index
 // (kx-1)*Ly + (ky-1).  Each row is split by the parity X = z0 & 1 of
 // z0 = kz-1 into two arrays of n = Lz/2 sites, site j of array X being
-// z0 = 2j + X.  An array is W = ceil(n/32) 32-bit words; the film's words are
-// laid out [X][row][w] (one "plane" per parity, rows contiguous, z fastest).
+// z0 = 2j + X.  An array is W = ceil(n/32) 32-bit words, stored with a row
+// stride of Wp = W rounded up to a multiple of 4 words (16 bytes, so a thread
+// moves four words with one 128-bit access; the extra words stay 0).  The
+// film's words are laid out [X][row][w] (one "plane" per parity, rows
+// contiguous, z fastest).
 // Inside a word, local site l (0..31) sits at bit (l >> 2) + 8*(l & 3), so the
 // four sites l = 4q..4q+3 served by one Philox call occupy bit q of each of
 // the four bytes.  Bit = 1 means S = +1.  Padding bits (j >= n) stay 0.
@@ -30,12 +33,13 @@ enum : uint32_t { kYGapbc = 0, kYPbc = 1, kYApbc = 2 };
 // `rec_next` are advanced by kernels so that captured graphs can be replayed.
 struct FilmDesc {
   uint32_t Lx, Ly, Lz, n, W;   // n = Lz/2 sites per array, W words per array
+  uint32_t Wp, nq;             // row stride in words (multiple of 4), nq = Wp / 4
   uint32_t y_mode, x_pbc;
   uint32_t key0, key1;         // Philox key
   uint32_t last_mask;          // valid bits of word W-1
   uint32_t last_calls;         // Philox calls needed by word W-1 (1..8)
   uint32_t upd_block_begin;    // first block of this film in the update grid
-  uint32_t upd_items;          // Lx*(Ly-1)*W
+  uint32_t upd_items;          // Lx*(Ly-1)*W (one item = one word of a row)
   uint32_t meas_block_begin;   // first block in the measurement grid
   uint32_t meas_bpl;           // measurement blocks per layer
   uint32_t measure_every;      // 0 = never
@@ -47,9 +51,21 @@ struct FilmDesc {
   uint64_t spin_off;           // word offset of plane X=0 in the spin pool
   uint64_t rec_off;            // int64 offset of the record ring
   uint64_t part_off;           // int64 offset of this film's partial sums
+  uint32_t divw_m, divw_l;     // n / W = (umulhi(n, m) + n) >> l  (n < 2^31)
+  uint32_t divy_m, divy_l;     // the same for Ly - 1
   uint32_t thr[4][16];         // Metropolis thresholds [class][s + 2*n_aligned]
   uint32_t always[4];          // bit (s + 2*n_aligned): accept without a draw
+  uint32_t reserved[2];
 };
+
+// Division by a runtime constant d < 2^31 for numerators n < 2^31 (round-up
+// multiplier: l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1).
+inline void fastdiv_magic(uint32_t d, uint32_t* m, uint32_t* l) {
+  uint32_t k = 0;
+  while ((1ull << k) < d) k++;
+  *l = k;
+  *m = (uint32_t)(((1ull << 32) * ((1ull << k) - d)) / d + 1);
+}
 
 // Work sizes of a launch, read by the kernels from device memory so that a
 // captured chunk can be replayed while films come and go.
@@ -71,6 +87,8 @@ __host__ __device__ inline uint32_t bitpos(uint32_t l) { return (l >> 2) + 8u * 
 #ifdef __CUDACC__
 
 __device__ __forceinline__ uint32_t mulhi(uint32_t a, uint32_t b) { return __umulhi(a, b); }
+
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, uint32_t m, uint32_t l) { return (__umulhi(n, m) + n) >> l; }
 
 // Philox4x32-10 (Salmon et al., SC'11) for counter (c0,c1,c2,c3), key (k0,k1).
 __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -114,17 +132,45 @@ struct PhiloxRow {
     r2_c0 = hi1b ^ x1 ^ k0b;
     r2_c1 = lo1b;
   }
+  // Two Philox calls (counter words 1 = c1a and c1b) computed side by side.
+  __device__ __forceinline__ void draw2(uint32_t c1a, uint32_t c1b, uint32_t oa[4], uint32_t ob[4]) const {
+    const uint32_t k1b = k1 + kWeyl1;
+    const uint32_t xa = r1_hi1 ^ c1a ^ k0, xb = r1_hi1 ^ c1b ^ k0;
+    const uint64_t pa = (uint64_t)kPhiloxM0 * xa, pb = (uint64_t)kPhiloxM0 * xb;
+    uint32_t a0 = r2_c0, a1 = r2_c1, a2 = (uint32_t)(pa >> 32) ^ r1_c3 ^ k1b, a3 = (uint32_t)pa;
+    uint32_t b0 = r2_c0, b1 = r2_c1, b2 = (uint32_t)(pb >> 32) ^ r1_c3 ^ k1b, b3 = (uint32_t)pb;
+    uint32_t kk0 = k0 + 2u * kWeyl0, kk1 = k1 + 2u * kWeyl1;
+#pragma unroll
+    for (int r = 2; r < 10; r++) {
+      const uint64_t pa0 = (uint64_t)kPhiloxM0 * a0, pa1 = (uint64_t)kPhiloxM1 * a2;
+      const uint64_t pb0 = (uint64_t)kPhiloxM0 * b0, pb1 = (uint64_t)kPhiloxM1 * b2;
+      a0 = (uint32_t)(pa1 >> 32) ^ a1 ^ kk0;
+      a1 = (uint32_t)pa1;
+      a2 = (uint32_t)(pa0 >> 32) ^ a3 ^ kk1;
+      a3 = (uint32_t)pa0;
+      b0 = (uint32_t)(pb1 >> 32) ^ b1 ^ kk0;
+      b1 = (uint32_t)pb1;
+      b2 = (uint32_t)(pb0 >> 32) ^ b3 ^ kk1;
+      b3 = (uint32_t)pb0;
+      kk0 += kWeyl0;
+      kk1 += kWeyl1;
+    }
+    oa[0] = a0; oa[1] = a1; oa[2] = a2; oa[3] = a3;
+    ob[0] = b0; ob[1] = b1; ob[2] = b2; ob[3] = b3;
+  }
   // Full Philox4x32-10 output for counter word 1 = c1.
   __device__ __forceinline__ void draw(uint32_t c1, uint32_t out[4]) const {
     uint32_t x0 = r1_hi1 ^ c1 ^ k0;  // end of round 1 (x1 = lo1, x2 = r1_x2, x3 = r1_c3)
     uint32_t k1b = k1 + kWeyl1;
-    uint32_t lo0 = kPhiloxM0 * x0, hi0 = mulhi(kPhiloxM0, x0);
+    const uint64_t pp = (uint64_t)kPhiloxM0 * x0;
+    const uint32_t lo0 = (uint32_t)pp, hi0 = (uint32_t)(pp >> 32);
     uint32_t c0 = r2_c0, c1w = r2_c1, c2 = hi0 ^ r1_c3 ^ k1b, c3 = lo0;  // end of round 2
     uint32_t kk0 = k0 + 2u * kWeyl0, kk1 = k1 + 2u * kWeyl1;
 #pragma unroll
     for (int r = 2; r < 10; r++) {
-      uint32_t l0 = kPhiloxM0 * c0, h0 = mulhi(kPhiloxM0, c0);
-      uint32_t l1 = kPhiloxM1 * c2, h1 = mulhi(kPhiloxM1, c2);
+      const uint64_t p0 = (uint64_t)kPhiloxM0 * c0, p1 = (uint64_t)kPhiloxM1 * c2;
+      const uint32_t l0 = (uint32_t)p0, h0 = (uint32_t)(p0 >> 32);
+      const uint32_t l1 = (uint32_t)p1, h1 = (uint32_t)(p1 >> 32);
       c0 = h1 ^ c1w ^ kk0;
       c1w = l1;
       c2 = h0 ^ c3 ^ kk1;

@@ -36,7 +36,7 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
 void build_tables(FilmDesc& d, double J, double H, double H1, double T);
 
 // Packed words of one film (both parity planes).
-inline size_t film_words(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.Ly * d.W; }
+inline size_t film_words(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.Ly * d.Wp; }
 inline size_t record_len(const FilmDesc& d) { return 5 + (size_t)d.Lx; }
 inline size_t part_len(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.meas_bpl; }
 

@@ -28,67 +28,70 @@ __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
 struct FilmCtx {
   uint32_t* plane0;
   uint32_t* plane1;
-  uint32_t Lx, Ly, n, W, y_mode, x_pbc, key0, key1, last_mask, last_calls;
+  uint32_t Lx, Ly, n, W, Wp, y_mode, x_pbc, key0, key1, last_mask, last_calls;
   uint32_t colour, sweep;
 };
 
-// Update word w of row (kx, ky): Metropolis decisions for its up to 32 sites.
-__device__ __forceinline__ void update_word(const FilmCtx& c, uint32_t kx, uint32_t ky, uint32_t w,
-                                            const uint32_t* __restrict__ s_thr,
-                                            const uint32_t* __restrict__ s_alw) {
-  const uint32_t Lx = c.Lx, Ly = c.Ly, W = c.W;
+// The words one thread needs to update word w of row (kx, ky), loaded ahead
+// of the arithmetic so that the loads of the next word overlap the current
+// word's Philox draws.
+struct Fetched {
+  uint32_t S, xm, xp, ym, yp, z0, za, zf;
+  uint32_t kx, ky, w;
+};
+
+__device__ __forceinline__ void fetch_word(const FilmCtx& c, uint32_t kx, uint32_t ky, uint32_t w, Fetched& f) {
+  const uint32_t Lx = c.Lx, Ly = c.Ly, W = c.W, Wp = c.Wp;
   const uint32_t row = (kx - 1) * Ly + (ky - 1);
   const uint32_t X = (kx + ky + 1 + c.colour) & 1u;
-  uint32_t* __restrict__ P = X ? c.plane1 : c.plane0;
+  const uint32_t* __restrict__ P = X ? c.plane1 : c.plane0;
   const uint32_t* __restrict__ Q = X ? c.plane0 : c.plane1;
-  const size_t rowW = (size_t)W;
-  const size_t base = (size_t)row * rowW + w;
-  const uint32_t S = P[base];
-
-  // x neighbours (free surfaces: an empty slot counts as not aligned)
-  uint32_t a0, a1, a2, a3, a4, a5;
-  if (kx > 1) a0 = ~(S ^ P[base - (size_t)Ly * rowW]);
-  else a0 = c.x_pbc ? ~(S ^ P[base + (size_t)(Lx - 1) * Ly * rowW]) : 0u;
-  if (kx < Lx) a1 = ~(S ^ P[base + (size_t)Ly * rowW]);
-  else a1 = c.x_pbc ? ~(S ^ P[base - (size_t)(Lx - 1) * Ly * rowW]) : 0u;
-  // y neighbours; the wrap rows follow Eq. 11 (reflected layer, sign reversed)
-  const bool neg = c.y_mode != kYPbc;
+  const uint32_t rbase = row * Wp;  // planes hold < 2^31 words
+  const uint32_t base = rbase + w;
+  const uint32_t LyWp = Ly * Wp;
   const uint32_t gkx = (c.y_mode == kYGapbc) ? (Lx - kx) : (kx - 1);  // 0-based layer of the wrap row
-  if (ky > 1) {
-    a2 = ~(S ^ P[base - rowW]);
-  } else {
-    uint32_t N = P[((size_t)gkx * Ly + (Ly - 1)) * rowW + w];
-    a2 = neg ? (S ^ N) : ~(S ^ N);
-  }
-  if (ky < Ly) {
-    a3 = ~(S ^ P[base + rowW]);
-  } else {
-    uint32_t N = P[((size_t)gkx * Ly) * rowW + w];
-    a3 = neg ? (S ^ N) : ~(S ^ N);
-  }
-  // z neighbours from the other parity of the same row (periodic in z)
-  const size_t rbase = (size_t)row * rowW;
-  const uint32_t Z0 = Q[base];
+  f.kx = kx; f.ky = ky; f.w = w;
+  f.S = P[base];
+  f.xm = (kx > 1) ? P[base - LyWp] : (c.x_pbc ? P[base + (Lx - 1) * LyWp] : 0u);
+  f.xp = (kx < Lx) ? P[base + LyWp] : (c.x_pbc ? P[base - (Lx - 1) * LyWp] : 0u);
+  f.ym = (ky > 1) ? P[base - Wp] : P[(gkx * Ly + (Ly - 1)) * Wp + w];
+  f.yp = (ky < Ly) ? P[base + Wp] : P[gkx * LyWp + w];
+  f.z0 = Q[base];
+  if (X == 0) f.za = (w > 0) ? Q[base - 1] : Q[rbase + W - 1];  // previous word, or the row's last
+  else f.za = (w + 1 < W) ? Q[base + 1] : Q[rbase];              // next word, or the row's first
+  f.zf = Q[rbase];
+}
+
+// Metropolis decisions for the up to 32 sites of the fetched word; returns
+// the new word.
+template <bool FULL>
+__device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched& f,
+                                                const uint32_t* __restrict__ s_thr,
+                                                const uint32_t* __restrict__ s_alw) {
+  const uint32_t Lx = c.Lx, Ly = c.Ly, W = c.W;
+  const uint32_t kx = f.kx, ky = f.ky, w = f.w;
+  const uint32_t row = (kx - 1) * Ly + (ky - 1);
+  const uint32_t X = (kx + ky + 1 + c.colour) & 1u;
+  const uint32_t S = f.S;
+  // aligned-with-S masks of the six neighbour slots (free x surface: empty
+  // slot, mask 0; Eq. 11 wrap: the partner's spin enters with reversed sign)
+  const uint32_t xm_on = (kx > 1 || c.x_pbc) ? 0xFFFFFFFFu : 0u;
+  const uint32_t xp_on = (kx < Lx || c.x_pbc) ? 0xFFFFFFFFu : 0u;
+  const uint32_t negm = (c.y_mode != kYPbc) ? 0xFFFFFFFFu : 0u;
+  const uint32_t a0 = ~(S ^ f.xm) & xm_on;
+  const uint32_t a1 = ~(S ^ f.xp) & xp_on;
+  const uint32_t a2 = ~(S ^ f.ym ^ (ky > 1 ? 0u : negm));
+  const uint32_t a3 = ~(S ^ f.yp ^ (ky < Ly ? 0u : negm));
   uint32_t Zs;
   if (X == 0) {
-    uint32_t pw;
-    if (w > 0) {
-      pw = Q[base - 1];
-    } else {
-      const uint32_t lastw = Q[rbase + W - 1];
-      pw = ((lastw >> bitpos((c.n - 1) & 31u)) & 1u) << 31;
-    }
-    Zs = shift_prev(Z0, pw);
+    const uint32_t pw = (w > 0) ? f.za : (((f.za >> bitpos((c.n - 1) & 31u)) & 1u) << 31);
+    Zs = shift_prev(f.z0, pw);
   } else {
-    const uint32_t nw = (w + 1 < W) ? Q[base + 1] : Q[rbase];
-    Zs = shift_next(Z0, nw);
-    if (w + 1 == W && c.last_mask != 0xFFFFFFFFu) {
-      const uint32_t r = (c.n - 1) & 31u;  // last valid local site of the last word
-      Zs |= (Q[rbase] & 1u) << bitpos(r);
-    }
+    Zs = shift_next(f.z0, f.za);
+    if (!FULL) Zs |= (f.zf & 1u) << bitpos((c.n - 1) & 31u);
   }
-  a4 = ~(S ^ Z0);
-  a5 = ~(S ^ Zs);
+  const uint32_t a4 = ~(S ^ f.z0);
+  const uint32_t a5 = ~(S ^ Zs);
 
   // bit-sliced count of aligned neighbours: n = c0 + 2 c1 + 4 c2
   const uint32_t s1 = a0 ^ a1 ^ a2, k1 = maj3(a0, a1, a2);
@@ -98,21 +101,22 @@ __device__ __forceinline__ void update_word(const FilmCtx& c, uint32_t kx, uint3
 
   const uint32_t cls = row_class(kx, Lx);
   // "always accept" (dE <= 0) as a 4-input function of (S, c0, c1, c2)
-  const uint32_t* m = s_alw + cls * 16;
-  uint32_t v0 = (S & m[1]) | (~S & m[0]);
-  uint32_t v1 = (S & m[3]) | (~S & m[2]);
-  uint32_t v2 = (S & m[5]) | (~S & m[4]);
-  uint32_t v3 = (S & m[7]) | (~S & m[6]);
-  uint32_t v4 = (S & m[9]) | (~S & m[8]);
-  uint32_t v5 = (S & m[11]) | (~S & m[10]);
-  uint32_t v6 = (S & m[13]) | (~S & m[12]);
-  uint32_t v7 = (S & m[15]) | (~S & m[14]);
-  uint32_t w0 = (c0 & v1) | (~c0 & v0);
-  uint32_t w1 = (c0 & v3) | (~c0 & v2);
-  uint32_t w2 = (c0 & v5) | (~c0 & v4);
-  uint32_t w3 = (c0 & v7) | (~c0 & v6);
-  uint32_t x0 = (c1 & w1) | (~c1 & w0);
-  uint32_t x1 = (c1 & w3) | (~c1 & w2);
+  const uint4* m4 = reinterpret_cast<const uint4*>(s_alw + cls * 16);
+  const uint4 ma = m4[0], mb = m4[1], mc = m4[2], md = m4[3];
+  const uint32_t v0 = (S & ma.y) | (~S & ma.x);
+  const uint32_t v1 = (S & ma.w) | (~S & ma.z);
+  const uint32_t v2 = (S & mb.y) | (~S & mb.x);
+  const uint32_t v3 = (S & mb.w) | (~S & mb.z);
+  const uint32_t v4 = (S & mc.y) | (~S & mc.x);
+  const uint32_t v5 = (S & mc.w) | (~S & mc.z);
+  const uint32_t v6 = (S & md.y) | (~S & md.x);
+  const uint32_t v7 = (S & md.w) | (~S & md.z);
+  const uint32_t w0 = (c0 & v1) | (~c0 & v0);
+  const uint32_t w1 = (c0 & v3) | (~c0 & v2);
+  const uint32_t w2 = (c0 & v5) | (~c0 & v4);
+  const uint32_t w3 = (c0 & v7) | (~c0 & v6);
+  const uint32_t x0 = (c1 & w1) | (~c1 & w0);
+  const uint32_t x1 = (c1 & w3) | (~c1 & w2);
   const uint32_t alw = (c2 & x1) | (~c2 & x0);
 
   // transpose the planes (S, c0, c1, c2) into nibbles: nibble r of U[a] holds
@@ -127,72 +131,170 @@ __device__ __forceinline__ void update_word(const FilmCtx& c, uint32_t kx, uint3
   U[2] = ((T0 >> 2) & 0x33333333u) | (T2 & 0xCCCCCCCCu);
   U[3] = ((T1 >> 2) & 0x33333333u) | (T3 & 0xCCCCCCCCu);
 
-  const bool last = (w + 1 == W);
-  const uint32_t ncalls = last ? c.last_calls : 8u;
-  const uint32_t valid = last ? c.last_mask : 0xFFFFFFFFu;
+  const uint32_t ncalls = FULL ? 8u : c.last_calls;
   const uint32_t clsb = (cls * 64u) * 0x01010101u;  // byte offset of this class's table
   const char* tb = reinterpret_cast<const char*>(s_thr);
   const PhiloxRow pr(row, c.sweep, X, c.key0, c.key1);
   uint32_t lt = 0;
+  // calls q and q + 4 are drawn together (two independent Philox chains)
 #pragma unroll
-  for (uint32_t q = 0; q < 8; q++) {
-    if (q < ncalls) {
-      uint32_t u[4];
-      pr.draw(8u * w + q, u);
-      const uint32_t Y = (q < 4 ? ((U[q & 3] << 2) & 0x3C3C3C3Cu) : ((U[q & 3] >> 2) & 0x3C3C3C3Cu)) | clsb;
+  for (uint32_t q = 0; q < 4; q++) {
+    if (FULL || q < ncalls) {
+      uint32_t u[4], v[4];
+      pr.draw2(8u * w + q, 8u * w + q + 4, u, v);
+      const bool two = FULL || q + 4 < ncalls;
+      const uint32_t Y = ((U[q] << 2) & 0x3C3C3C3Cu) | clsb;
+      const uint32_t Y2 = ((U[q] >> 2) & 0x3C3C3C3Cu) | clsb;
 #pragma unroll
       for (uint32_t i = 0; i < 4; i++) {
-        const uint32_t off = (Y >> (8 * i)) & 0xFFu;
-        const uint32_t t = *reinterpret_cast<const uint32_t*>(tb + off);
+        const uint32_t t = *reinterpret_cast<const uint32_t*>(tb + ((Y >> (8 * i)) & 0xFFu));
         if (u[i] < t) lt |= 1u << (q + 8 * i);
+        const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + ((Y2 >> (8 * i)) & 0xFFu));
+        if (two && v[i] < t2) lt |= 1u << (q + 4 + 8 * i);
       }
     }
   }
-  const uint32_t flip = (lt | alw) & valid;
-  P[base] = S ^ flip;
+  const uint32_t valid = FULL ? 0xFFFFFFFFu : c.last_mask;
+  return S ^ ((lt | alw) & valid);
+}
+
+__device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, uint32_t v) {
+  const uint32_t row = (f.kx - 1) * c.Ly + (f.ky - 1);
+  const uint32_t X = (f.kx + f.ky + 1 + c.colour) & 1u;
+  uint32_t* __restrict__ P = X ? c.plane1 : c.plane0;
+  P[row * c.Wp + f.w] = v;
+}
+
+__device__ __forceinline__ void item_word(const FilmCtx& c, uint32_t item, uint32_t dwm, uint32_t dwl,
+                                          uint32_t dym, uint32_t dyl, uint32_t& kx, uint32_t& ky, uint32_t& w) {
+  const uint32_t rp = fastdiv(item, dwm, dwl);
+  w = item - rp * c.W;
+  const uint32_t kxm1 = fastdiv(rp, dym, dyl);
+  ky = rp - kxm1 * (c.Ly - 1) + 1;
+  kx = kxm1 + 1;
+}
+
+__device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
+                                               const uint32_t* s_alw) {
+  const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
+  const uint32_t v = full ? decide_word<true>(c, f, s_thr, s_alw) : decide_word<false>(c, f, s_thr, s_alw);
+  store_word(c, f, v);
+  // ky = 1 rows then update their wrap partner row (kx', Ly); its wrap
+  // neighbour is the word just written, so it is fetched only now
+  if (f.ky == 1) {
+    const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
+    Fetched g;
+    fetch_word(c, kx2, c.Ly, f.w, g);
+    const uint32_t v2 = full ? decide_word<true>(c, g, s_thr, s_alw) : decide_word<false>(c, g, s_thr, s_alw);
+    store_word(c, g, v2);
+  }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kUpdateBlock)
+// Persistent half-sweep: block b walks a contiguous run of virtual blocks
+// (128 words each) and, while the arithmetic of one word runs, already holds
+// the neighbour words of the next one.
+__global__ void __launch_bounds__(kUpdateBlock, kUpdateMinBlocks)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k) {
-  __shared__ uint32_t s_thr[64];
-  __shared__ uint32_t s_alw[64];
+  constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
+  static_assert(sizeof(FilmDesc) % 16 == 0, "descriptor copied as uint4");
+  __shared__ __align__(16) FilmDesc s_d;
+  __shared__ __align__(16) uint32_t s_alw[64];
   const uint32_t nvb = hdr->upd_blocks;
+  const uint32_t per = (nvb + gridDim.x - 1) / gridDim.x;
+  const uint32_t vb_end = min(nvb, (blockIdx.x + 1) * per);
   uint32_t cur = 0xFFFFFFFFu;
-  for (uint32_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+  FilmCtx c;
+  uint32_t dwm = 0, dwl = 0, dym = 0, dyl = 0;
+  bool run = false;
+  Fetched nxt;
+  bool have = false;
+  for (uint32_t vb = blockIdx.x * per; vb < vb_end; vb++) {
     const uint32_t f = owner[vb];  // the same for every thread of the block
-    const FilmDesc& F = films[f];
     if (f != cur) {
       __syncthreads();
-      for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
-        s_thr[i] = F.thr[i >> 4][i & 15];
-        s_alw[i] = ((F.always[i >> 4] >> (i & 15)) & 1u) ? 0xFFFFFFFFu : 0u;
-      }
+      const uint4* src = reinterpret_cast<const uint4*>(films + f);
+      uint4* dst = reinterpret_cast<uint4*>(&s_d);
+      for (uint32_t i = threadIdx.x; i < kDescWords / 4; i += blockDim.x) dst[i] = src[i];
+      for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x)
+        s_alw[i] = ((films[f].always[i >> 4] >> (i & 15)) & 1u) ? 0xFFFFFFFFu : 0u;
       __syncthreads();
       cur = f;
+      have = false;
+      run = s_d.active && s_d.sweep + k < s_d.sweep_end;
+      c.Lx = s_d.Lx; c.Ly = s_d.Ly; c.n = s_d.n; c.W = s_d.W; c.Wp = s_d.Wp;
+      c.y_mode = s_d.y_mode; c.x_pbc = s_d.x_pbc; c.key0 = s_d.key0; c.key1 = s_d.key1;
+      c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
+      c.colour = colour; c.sweep = s_d.sweep + k;
+      c.plane0 = pool + s_d.spin_off;
+      c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
+      dwm = s_d.divw_m; dwl = s_d.divw_l; dym = s_d.divy_m; dyl = s_d.divy_l;
     }
-    if (!F.active || F.sweep + k >= F.sweep_end) continue;
-    const uint32_t item = (vb - F.upd_block_begin) * blockDim.x + threadIdx.x;
-    if (item >= F.upd_items) continue;
-    FilmCtx c;
-    c.Lx = F.Lx; c.Ly = F.Ly; c.n = F.n; c.W = F.W;
-    c.y_mode = F.y_mode; c.x_pbc = F.x_pbc; c.key0 = F.key0; c.key1 = F.key1;
-    c.last_mask = F.last_mask; c.last_calls = F.last_calls;
-    c.colour = colour; c.sweep = F.sweep + k;
-    c.plane0 = pool + F.spin_off;
-    c.plane1 = c.plane0 + (size_t)F.Lx * F.Ly * F.W;
-    const uint32_t w = item % c.W;
-    const uint32_t rp = item / c.W;
-    const uint32_t kx = rp / (c.Ly - 1) + 1;
-    const uint32_t ky = rp % (c.Ly - 1) + 1;
-    update_word(c, kx, ky, w, s_thr, s_alw);
-    if (ky == 1) {
-      const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - kx) : kx;
-      update_word(c, kx2, c.Ly, w, s_thr, s_alw);
+    if (!run) continue;
+    const uint32_t first = s_d.upd_block_begin, items = s_d.upd_items;
+    const uint32_t item = (vb - first) * kUpdateBlock + threadIdx.x;
+    Fetched cw;
+    const bool mine = item < items;
+    if (have) {
+      cw = nxt;
+    } else if (mine) {
+      uint32_t kx, ky, w;
+      item_word(c, item, dwm, dwl, dym, dyl, kx, ky, w);
+      fetch_word(c, kx, ky, w, cw);
+    }
+    // fetch the next virtual block's word now if it belongs to the same film
+    have = false;
+    if (vb + 1 < vb_end && owner[vb + 1] == f) {
+      const uint32_t item2 = item + kUpdateBlock;
+      if (item2 < items) {
+        uint32_t kx, ky, w;
+        item_word(c, item2, dwm, dwl, dym, dyl, kx, ky, w);
+        fetch_word(c, kx, ky, w, nxt);
+        have = true;
+      }
+    }
+    if (mine) update_fetched(c, cw, &s_d.thr[0][0], s_alw);
+  }
+}
+
+// Single-film half-sweep.  The descriptor is a __grid_constant__ kernel
+// parameter, so every per-film constant is read straight from the constant
+// bank; each thread updates kFilmItems words, kFilmThreads words apart.
+__global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
+update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
+                   uint32_t sweep) {
+  __shared__ __align__(16) uint32_t s_thr[64];
+  __shared__ __align__(16) uint32_t s_alw[64];
+  for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
+    s_thr[i] = d.thr[i >> 4][i & 15];
+    s_alw[i] = ((d.always[i >> 4] >> (i & 15)) & 1u) ? 0xFFFFFFFFu : 0u;
+  }
+  __syncthreads();
+  FilmCtx c;
+  c.Lx = d.Lx; c.Ly = d.Ly; c.n = d.n; c.W = d.W; c.Wp = d.Wp;
+  c.y_mode = d.y_mode; c.x_pbc = d.x_pbc; c.key0 = d.key0; c.key1 = d.key1;
+  c.last_mask = d.last_mask; c.last_calls = d.last_calls;
+  c.colour = colour; c.sweep = sweep;
+  c.plane0 = pool + d.spin_off;
+  c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
+  const uint32_t base = blockIdx.x * (kFilmThreads * kFilmItems) + threadIdx.x;
+  Fetched fw[kFilmItems];
+  bool mine[kFilmItems];
+#pragma unroll
+  for (uint32_t it = 0; it < kFilmItems; it++) {
+    const uint32_t item = base + it * kFilmThreads;
+    mine[it] = item < d.upd_items;
+    if (mine[it]) {
+      uint32_t kx, ky, w;
+      item_word(c, item, d.divw_m, d.divw_l, d.divy_m, d.divy_l, kx, ky, w);
+      fetch_word(c, kx, ky, w, fw[it]);
     }
   }
+#pragma unroll
+  for (uint32_t it = 0; it < kFilmItems; it++)
+    if (mine[it]) update_fetched(c, fw[it], s_thr, s_alw);
 }
 
 // ------------------------------------------------------------ measurement
@@ -236,15 +338,16 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
     const uint32_t Lx = F.Lx, Ly = F.Ly, W = F.W, bpl = F.meas_bpl;
     const uint32_t local = vb - F.meas_block_begin;
     const uint32_t kxm1 = local / bpl, chunk = local % bpl;
+    const uint32_t Wp = F.Wp;
     const uint32_t* A = pool + F.spin_off;
-    const uint32_t* B = A + (size_t)Lx * Ly * W;
+    const uint32_t* B = A + (size_t)Lx * Ly * Wp;
     const bool neg = F.y_mode != kYPbc;
     const uint32_t gkx = (F.y_mode == kYGapbc) ? (Lx - 1 - kxm1) : kxm1;
     int64_t msum = 0, bsum = 0;
     for (uint32_t it = chunk * blockDim.x + threadIdx.x; it < Ly * W; it += bpl * blockDim.x) {
       const uint32_t kym1 = it / W, w = it % W;
       const uint32_t row = kxm1 * Ly + kym1;
-      const size_t base = (size_t)row * W + w;
+      const size_t base = (size_t)row * Wp + w;
       const bool last = (w + 1 == W);
       const uint32_t valid = last ? F.last_mask : 0xFFFFFFFFu;
       const int nv = __popc(valid);
@@ -253,23 +356,23 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
       int bb = 0;
       // +x bond
       if (kxm1 + 1 < Lx) {
-        const size_t nb = base + (size_t)Ly * W;
+        const size_t nb = base + (size_t)Ly * Wp;
         bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
       } else if (F.x_pbc) {
-        const size_t nb = base - (size_t)(Lx - 1) * Ly * W;
+        const size_t nb = base - (size_t)(Lx - 1) * Ly * Wp;
         bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
       }
       // +y bond (wrap: the Eq. 11 partner row, sign -1 unless PBC)
       if (kym1 + 1 < Ly) {
-        bb += bonds(a, A[base + W], valid, nv) + bonds(b, B[base + W], valid, nv);
+        bb += bonds(a, A[base + Wp], valid, nv) + bonds(b, B[base + Wp], valid, nv);
       } else {
-        const size_t g = ((size_t)gkx * Ly) * W + w;
+        const size_t g = ((size_t)gkx * Ly) * Wp + w;
         const int y = bonds(a, A[g], valid, nv) + bonds(b, B[g], valid, nv);
         bb += neg ? -y : y;
       }
       // +z bonds: (2j, 2j+1) inside the word pair, (2j+1, 2j+2) through a shift
       bb += bonds(a, b, valid, nv);
-      const size_t rbase = (size_t)row * W;
+      const size_t rbase = (size_t)row * Wp;
       uint32_t an = shift_next(a, last ? A[rbase] : A[base + 1]);
       if (last && F.last_mask != 0xFFFFFFFFu) an |= (A[rbase] & 1u) << bitpos((F.n - 1) & 31u);
       bb += bonds(b, an, valid, nv);
@@ -336,12 +439,16 @@ __global__ void advance_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __
 // ------------------------------------------------------------- set-up
 
 __global__ void init_kernel(FilmDesc F, uint32_t* __restrict__ pool, int kind, uint32_t flip_lo, int flip_all) {
-  const size_t words = (size_t)F.Lx * F.Ly * F.W;
+  const size_t words = (size_t)F.Lx * F.Ly * F.Wp;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * words) return;
   const uint32_t X = (uint32_t)(i / words);
   const size_t rem = i % words;
-  const uint32_t row = (uint32_t)(rem / F.W), w = (uint32_t)(rem % F.W);
+  const uint32_t row = (uint32_t)(rem / F.Wp), w = (uint32_t)(rem % F.Wp);
+  if (w >= F.W) {
+    pool[F.spin_off + i] = 0u;
+    return;
+  }
   const uint32_t ky = row % F.Ly + 1;
   const bool last = (w + 1 == F.W);
   const uint32_t valid = last ? F.last_mask : 0xFFFFFFFFu;
@@ -366,13 +473,13 @@ __global__ void init_kernel(FilmDesc F, uint32_t* __restrict__ pool, int kind, u
 
 // int8 canonical order -> packed planes
 __global__ void pack_kernel(FilmDesc F, uint32_t* __restrict__ pool, const int8_t* __restrict__ s) {
-  const size_t words = (size_t)F.Lx * F.Ly * F.W;
+  const size_t words = (size_t)F.Lx * F.Ly * F.Wp;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * words) return;
   const uint32_t X = (uint32_t)(i / words);
   const size_t rem = i % words;
-  const size_t row = rem / F.W;
-  const uint32_t w = (uint32_t)(rem % F.W);
+  const size_t row = rem / F.Wp;
+  const uint32_t w = (uint32_t)(rem % F.Wp);
   uint32_t word = 0;
   for (uint32_t l = 0; l < 32; l++) {
     const uint32_t j = 32u * w + l;
@@ -390,8 +497,8 @@ __global__ void unpack_kernel(FilmDesc F, const uint32_t* __restrict__ pool, int
   const size_t row = i / F.Lz;
   const uint32_t z0 = (uint32_t)(i % F.Lz);
   const uint32_t X = z0 & 1u, j = z0 >> 1;
-  const size_t words = (size_t)F.Lx * F.Ly * F.W;
-  const uint32_t word = pool[F.spin_off + X * words + row * F.W + (j >> 5)];
+  const size_t words = (size_t)F.Lx * F.Ly * F.Wp;
+  const uint32_t word = pool[F.spin_off + X * words + row * F.Wp + (j >> 5)];
   s[i] = ((word >> bitpos(j & 31u)) & 1u) ? (int8_t)1 : (int8_t)-1;
 }
 
@@ -401,6 +508,15 @@ cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uin
                           cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
   update_kernel<<<grid, kUpdateBlock, 0, st>>>(L.films, L.owner_upd, L.hdr, pool, colour, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep,
+                               cudaStream_t st) {
+  const uint32_t per = kFilmThreads * kFilmItems;
+  const uint32_t grid = (d.upd_items + per - 1) / per;
+  if (grid == 0) return cudaSuccess;
+  update_film_kernel<<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
   return cudaGetLastError();
 }
 
@@ -423,13 +539,13 @@ cudaError_t launch_advance(const LaunchSet& L, uint32_t grid, uint32_t n_sweeps,
 
 cudaError_t launch_init(const FilmDesc& f, uint32_t* pool, int kind, uint32_t flip_lo, int flip_all,
                         cudaStream_t st) {
-  const size_t n = 2 * (size_t)f.Lx * f.Ly * f.W;
+  const size_t n = 2 * (size_t)f.Lx * f.Ly * f.Wp;
   init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, pool, kind, flip_lo, flip_all);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const FilmDesc& f, uint32_t* pool, const int8_t* s, cudaStream_t st) {
-  const size_t n = 2 * (size_t)f.Lx * f.Ly * f.W;
+  const size_t n = 2 * (size_t)f.Lx * f.Ly * f.Wp;
   pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, pool, s);
   return cudaGetLastError();
 }

@@ -9,6 +9,12 @@
 namespace isg {
 
 constexpr int kUpdateBlock = 128;
+constexpr int kUpdateMinBlocks = 5;
+
+// Single-film kernel: threads per block, words per thread, blocks per SM.
+constexpr uint32_t kFilmThreads = 128;
+constexpr uint32_t kFilmItems = 2;
+constexpr int kFilmMinBlocks = 6;
 constexpr int kMeasureBlock = 256;
 
 // Items a measurement block covers per layer before another block is added.
@@ -24,6 +30,10 @@ struct LaunchSet {
 
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k,
                           cudaStream_t st);
+// One half-sweep of a single film whose descriptor (with `sweep` absolute) is
+// passed by value.
+cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep,
+                               cudaStream_t st);
 cudaError_t launch_measure(const LaunchSet& L, uint32_t grid, uint32_t fin_grid, const uint32_t* pool,
                            int64_t* part, int64_t* records, uint32_t done, int force, int64_t* direct,
                            cudaStream_t st);
