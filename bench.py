@@ -1,0 +1,377 @@
+"""Benchmark of the Ising-film sweep on GB300: spin-flip attempts per ns.
+
+One step = 10 checkerboard Metropolis sweeps of the 120 x 240 x 1600 film
+(46,080,000 spins, Eq. 11 boundary, H1 = +0.55, T = 3) plus one record of the
+int64 sums B, M, M1, Mn, m(kx) -- the film and cadence of the paper-scale run.
+The default run times 200 steps (the 2000 sweeps of that run) after 3 warm-up
+steps, flushing L2 between steps, and prints one JSON line with the roofline
+of the update kernel, the oracle's CPU rate, an end-to-end figure through
+host buffers, clocks, and bounded batched/serving runs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs its own replica of the film (independent
+chains, no collective: weak scaling); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/ns on 1 GB300, batched vs plain, % roofline; p99 latency"
+UNIT = "attempts/ns"
+SWEEPS_PER_STEP = 10
+# Algorithmic integer work per attempt: Philox4x32-10 shared by 4 sites
+# (10 rounds x (2 mul-hi + 2 mul-lo + 4 xor) + 9 x 2 key adds = 98 ops) = 24.5,
+# plus neighbour count (1), threshold select/compare (3), flip (1): 29.5 -> 30.
+OPS_PER_ATTEMPT = 30
+# INT32 peak: 152 SMs x 4 schedulers x 32 lanes (one warp instruction per
+# scheduler per cycle) x 2.07 GHz maximum SM clock.
+N_SM, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
+PROFILE = os.path.join(ROOT, "profiles", "update_film_kernel_film46m.md")
+KERNEL_SOURCES = ["paper_1411_5588_gb300/csrc/ising_kernels.cu", "paper_1411_5588_gb300/csrc/ising_device.cuh",
+                  "paper_1411_5588_gb300/csrc/ising_launch.h"]
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """dram bytes per update launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel-source-sha1:\s*([0-9a-f]{40})", text)
+    t = re.search(r"dram-bytes-per-launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.gpu], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def cpu_baseline(min_seconds=10.0, max_sweeps=40):
+    """The oracle, as it stands, on the host cores: sweeps of the 46M-site
+    film after its slab start, until about min_seconds of CPU work."""
+    from oracle import oracle as O
+    from paper_1411_5588_gb300 import workloads as WL
+    job = WL.film_46m()
+    ncores = os.cpu_count() or 1
+    O.set_threads(ncores)
+    f = O.Film(job["Lx"], job["Ly"], job["Lz"], job["J"], job["H1"], job["T"], job["seed"])
+    f.init(O.INIT_SLAB_Y, job["flip_p"])
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_sweeps and (n == 0 or time.perf_counter() - t0 < min_seconds):
+        f.sweep(1, 0)
+        n += 1
+    dt = time.perf_counter() - t0
+    att = WL.sites(job) * n
+    return {"value": att / dt / 1e9, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": f"{n} sweeps of the 120x240x1600 film after its slab start ({att} attempts, {dt:.1f} s)"}
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle on the host cores, one sweep of the
+    46M-site film per step (a bounded sample of a 10-sweep step)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1411_5588_gb300 import workloads as WL
+    job = WL.film_46m()
+    O.set_threads(os.cpu_count() or 1)
+    f = O.Film(job["Lx"], job["Ly"], job["Lz"], job["J"], job["H1"], job["T"], job["seed"])
+    f.init(O.INIT_SLAB_Y, job["flip_p"])
+    for _ in range(args.warmup):
+        f.sweep(1, 0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f.sweep(1, 1)
+    dt = time.perf_counter() - t0
+    att = WL.sites(job) * args.steps
+    value = att / dt / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "film 120x240x1600 (46,080,000 spins), Eq. 11 y boundary, H1=+0.55, T=3, "
+                                   "slab start + 1% flips, seed 2; one sweep + one record per step (CPU sample)",
+                       "parallelism": f"openmp x{O.get_threads()}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} sweeps of the 120x240x1600 film"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def batched_vs_plain(ig, WL, torch, sweeps=20):
+    """64-film integration set: one batch (shared launches, CUDA graph) vs the
+    same films run one after another through the single-film path.  Both
+    time sweeps only (creation and initial states excluded)."""
+    jobs = WL.ti_batch(n_sweeps=2 * sweeps)
+    for j in jobs:
+        j["measure_every"] = 10
+    per_sweep = sum(WL.sites(j) for j in jobs)
+    b = ig.Batch(jobs)
+    b.sweep(sweeps, True)  # warm-up (captures the graph)
+    b.synchronize()
+    t0 = time.perf_counter()
+    b.sweep(2 * sweeps, True)
+    b.synchronize()
+    tb = time.perf_counter() - t0
+    b.close()
+    batched = per_sweep * 2 * sweeps / tb / 1e9
+    tp = 0.0
+    for j in jobs:
+        g = ig.Film(j["Lx"], j["Ly"], j["Lz"], j["J"], j["H1"], j["T"], j["seed"], replica=j["replica"])
+        g.init(j["init_kind"])
+        g.synchronize()
+        t0 = time.perf_counter()
+        g.sweep(sweeps, 10)
+        g.synchronize()
+        tp += time.perf_counter() - t0
+        g.read_series()
+        g.close()
+    plain = per_sweep * sweeps / tp / 1e9
+    return {"workload": "64 films 32x64x128..96x192x384 (16 H1 nodes x 2 T x 2 seeds), records every 10 sweeps",
+            "batched": batched, "plain": plain, "ratio": batched / plain, "unit": UNIT,
+            "sweeps": {"batched": 2 * sweeps, "plain_per_film": sweeps}}
+
+
+def serving(ig, WL, n_jobs=2000, chunk=50, budget=16 << 30):
+    """Poisson stream of jobs into the continuous-batching server."""
+    jobs = WL.serve_2000(n_jobs=n_jobs)
+    srv = ig.Server(budget, chunk_sweeps=chunk)
+    t0 = time.perf_counter()
+    tickets = []
+    for j in jobs:
+        delay = j["arrival"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets += srv.submit([j])
+    lat = []
+    att = 0
+    for t, j in zip(tickets, jobs):
+        srv.wait(t, 3600.0)
+        _, _, info = srv.result(t, want_spins=False)
+        lat.append(info["t_finish"] - info["t_submit"])
+        att += WL.sites(j) * j["n_sweeps"]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat.sort()
+    q = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
+    return {"workload": f"{n_jobs} jobs, Poisson 200/s, sizes 16^3..96x192x768, 500-5000 sweeps",
+            "attempts_per_ns": att / wall / 1e9, "p50_latency_s": q(0.50), "p99_latency_s": q(0.99),
+            "wall_s": wall, "offered_attempts_per_ns": att / (jobs[-1]["arrival"] + 1e-9) / 1e9,
+            "chunk_sweeps": chunk, "chunks": st["chunks"]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched/serving/e2e/cpu legs")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    rank, world, local = dist_env()
+    cpu = None
+    if rank == 0 and not args.no_extras:
+        cpu = cpu_baseline()  # before any GPU work in this process
+    import torch
+    import paper_1411_5588_gb300 as ig
+    from paper_1411_5588_gb300 import workloads as WL
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    job = WL.film_46m(replica=rank)
+    stream = torch.cuda.Stream()
+    film = ig.Film(job["Lx"], job["Ly"], job["Lz"], job["J"], job["H1"], job["T"], job["seed"],
+                   replica=job["replica"], stream=stream)
+    film.init(job["init_kind"], job["flip_p"])
+    sites = WL.sites(job)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            film.sweep(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
+        film.synchronize()
+        film.read_series()
+        events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.4)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in events:
+            flush.fill_(1)  # evict L2 (inputs smaller than L2)
+            e0.record(stream)
+            film.sweep(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop()
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in events]
+        recs = film.read_series()
+        assert recs.shape[0] == args.steps, recs.shape
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = world * sites * SWEEPS_PER_STEP * args.steps / (total_ms * 1e6)
+
+        # update-kernel launch duration: sweeps without records are update
+        # launches only (plus one counter-advance launch)
+        n_k = 50
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        k0.record(stream)
+        film.sweep(n_k, 0)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        upd_ms = k0.elapsed_time(k1) / (2 * n_k)
+    ops_per_launch = OPS_PER_ATTEMPT * sites / 2
+    achieved = ops_per_launch / (upd_ms * 1e-3) / 1e12
+    peak = N_SM * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(), "kernel": "update_film_kernel",
+                "launch_us": upd_ms * 1e3, "ops_per_attempt": OPS_PER_ATTEMPT,
+                "peak_from": "152 SMs x 128 int32 lanes x 2.07 GHz (nominal max clock)",
+                "attempts_per_ns_at_peak": peak * 1e3 / OPS_PER_ATTEMPT}
+
+    e2e = None
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # end to end through the C ABI: initial lattice from pinned host memory,
+        # each step's record read back to host memory
+        host = torch.from_numpy(film.get_spins()).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lib = ig.lib()
+        ig.check(lib.ising_set_spins(film._h, ig.binding.P(host.data_ptr())), "ising_set_spins")
+        for _ in range(args.steps):
+            film.sweep(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
+            film.read_series()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": sites * SWEEPS_PER_STEP * args.steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": sites / args.steps, "d2h_bytes_per_step": 8 * (5 + job["Lx"]),
+               "note": "initial int8 lattice uploaded once from pinned memory (bytes spread over the steps); "
+                       "one record read back per step"}
+        for name, fn in (("batched", lambda: batched_vs_plain(ig, WL, torch)),
+                         ("serving", lambda: serving(ig, WL, n_jobs=args.serve_jobs))):
+            try:
+                extras[name] = fn()
+            except Exception as exc:  # report, never hide the main line
+                extras[name] = {"error": repr(exc)}
+    film.close()
+    if rank != 0:
+        return
+    per_step_launches = 2 * SWEEPS_PER_STEP + 2 + 1
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "film 120x240x1600 (46,080,000 spins, bit-packed), Eq. 11 y boundary, "
+                                   "free x with H1=+0.55/-0.55, periodic z, T=3, slab start + 1% flips, seed 2; "
+                                   "step = 10 sweeps + one int64 record",
+                       "sweeps_per_step": SWEEPS_PER_STEP, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "clocks": clocks, "gpu_launches": per_step_launches * args.steps,
+            "e2e": e2e, "cpu_baseline": cpu}
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
