@@ -251,6 +251,32 @@ int ising_ti_beta_trapezoid(int n, const double *beta, const double *U, double *
  * in T over n points (T[i], U[i]).  host. */
 int ising_ti_temperature_trapezoid(int n, const double *T, const double *U, double *out);
 
+/* ------------------------------------- measurement without allocation */
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: a framework or serving runtime whose own
+ * pool allocator already owns the device, or a loop that cannot take the
+ * implicit device synchronisation of cudaMalloc.  It computes the record
+ * {sweep, B, M, M1, Mn, m(1..Lx)} of a packed film exactly as
+ * ising_measure does, but allocates nothing.
+ *   spins   device, caller-owned: the film in the library's packed layout
+ *           (ising_packed_words() words, as written by
+ *           ising_get_packed_device).
+ *   Lx, Ly, Lz, y_mode, x_mode   the film's geometry (as for ising_create
+ *           and ising_set_options).
+ *   sweep   copied into record[0].
+ *   record  device, caller-owned: 5 + Lx int64, written asynchronously.
+ *   stream  cudaStream_t as void* (NULL = the default stream).
+ * The per-block partial sums go to one fixed 128 KiB device array inside the
+ * library (16384 int64), so the film may use at most 8192 measurement blocks,
+ * Lx * ceil(Ly * ceil(Lz / 64) / 1024) <= 8192; larger films get EINVAL.
+ * The first call on each device looks up that array's device address (do it
+ * before any stream capture).  All calls on a device share the array: each
+ * call overwrites every partial it reads, so nothing needs clearing, but
+ * calls whose kernels overlap on the GPU race on it. */
+int ising_measure_packed_noalloc(const uint32_t *spins, int Lx, int Ly, int Lz, int y_mode, int x_mode,
+                                 uint64_t sweep, int64_t *record, void *stream);
+
 /* ------------------------------------------------------------- misc */
 
 const char *ising_strerror(int status);

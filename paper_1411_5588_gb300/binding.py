@@ -93,6 +93,7 @@ _SIGS = {
     "ising_ti_surface_field": [_c.c_int, _c.c_double, P, P, DP],
     "ising_ti_beta_trapezoid": [_c.c_int, P, P, DP],
     "ising_ti_temperature_trapezoid": [_c.c_int, P, P, DP],
+    "ising_measure_packed_noalloc": [P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64, P, P],
     "ising_strerror": [_c.c_int],
     "ising_last_error": [],
     "ising_version": [_c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)],
