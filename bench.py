@@ -121,6 +121,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, device="cpu"):
+    """Maximum of a float over all ranks of the default process group (the
+    value itself when no group is initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -302,11 +314,7 @@ def main():
         step_ms = [e0.elapsed_time(e1) for e0, e1 in events]
         recs = film.read_series()
         assert recs.shape[0] == args.steps, recs.shape
-        total_ms = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(step_ms), device="cuda")
         value = world * sites * SWEEPS_PER_STEP * args.steps / (total_ms * 1e6)
 
         # update-kernel launch duration: sweeps without records are update

@@ -372,3 +372,31 @@ def test_one_layer_film_energy_matches_kaufman(y_mode, L, T):
     recs = f.sweep(60000, 1)
     mu, err = _binned_mean(recs[:, 1], nbins=40)
     assert abs(mu - want) < 4 * err, (mu, want, err)
+
+
+# ------------------------------------------------------------ initial states
+
+@pytest.mark.parametrize("p", [0.0, 0.01, 0.3, 1.0])
+def test_slab_start_is_a_slab_with_binomial_flips(p):
+    """SLAB_Y: +1 for ky <= Ly/2, -1 above, then each spin reversed with
+    probability p -- the flip count is Binomial(N, floor(p 2^32)/2^32)."""
+    Lx, Ly, Lz = 6, 11, 40
+    f = O.Film(Lx, Ly, Lz, 1.0, 0.0, 3.0, 17)
+    f.init(O.INIT_SLAB_Y, p)
+    s = f.get_spins().reshape(Lx, Ly, Lz)
+    slab = np.where(np.arange(1, Ly + 1) <= Ly // 2, 1, -1)[None, :, None]
+    flipped = int((s != slab).sum())
+    N = s.size
+    q = math.floor(math.ldexp(p, 32)) / 2 ** 32
+    if q in (0.0, 1.0):
+        assert flipped == round(q * N)
+    else:
+        sd = math.sqrt(N * q * (1 - q))
+        assert abs(flipped - N * q) < 5 * sd + 1
+
+
+def test_random_start_is_balanced():
+    f = O.Film(10, 12, 64, 1.0, 0.0, 3.0, 23)
+    f.init(O.INIT_RANDOM)
+    s = f.get_spins().astype(np.int64)
+    assert abs(s.sum()) < 5 * math.sqrt(s.size)
