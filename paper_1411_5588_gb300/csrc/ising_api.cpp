@@ -75,7 +75,11 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
 
 void build_tables(FilmDesc& d, double J, double H, double H1, double T) {
   const int Lx = (int)d.Lx;
+  d.has_never = 0;
   for (int cls = 0; cls < 4; cls++) {
+    bool present = false;  // does some layer kx have this class?
+    for (int kx = 1; kx <= Lx && !present; kx = (kx == 1 && Lx > 2) ? Lx - 1 : kx + 1)
+      present = row_class((uint32_t)kx, (uint32_t)Lx) == (uint32_t)cls;
     const bool first = cls & 1, lastl = (cls & 2) != 0;
     uint32_t always = 0;
     // classes that cannot occur for this Lx keep a harmless table
@@ -100,6 +104,7 @@ void build_tables(FilmDesc& d, double J, double H, double H1, double T) {
         continue;
       }
       d.thr[cls][idx] = (uint32_t)t;
+      if (t == 0.0 && present) d.has_never = 1;
     }
     d.always[cls] = always;
     (void)Lx;

@@ -55,7 +55,8 @@ struct FilmDesc {
   uint32_t divy_m, divy_l;     // the same for Ly - 1
   uint32_t thr[4][16];         // Metropolis thresholds [class][s + 2*n_aligned]
   uint32_t always[4];          // bit (s + 2*n_aligned): accept without a draw
-  uint32_t reserved[2];
+  uint32_t has_never;          // some reachable entry has dE > 0 and thr = 0
+  uint32_t reserved;
 };
 
 // Division by a runtime constant d < 2^31 for numerators n < 2^31 (round-up

@@ -64,7 +64,7 @@ __device__ __forceinline__ void fetch_word(const FilmCtx& c, uint32_t kx, uint32
 
 // Metropolis decisions for the up to 32 sites of the fetched word; returns
 // the new word.
-template <bool FULL>
+template <bool FULL, bool FAST>
 __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched& f,
                                                 const uint32_t* __restrict__ s_thr,
                                                 const uint32_t* __restrict__ s_alw) {
@@ -100,6 +100,8 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const uint32_t c1 = k1 ^ k2 ^ k3, c2 = maj3(k1, k2, k3);
 
   const uint32_t cls = row_class(kx, Lx);
+  uint32_t alw = 0;
+  if (!FAST) {
   // "always accept" (dE <= 0) as a 4-input function of (S, c0, c1, c2)
   const uint4* m4 = reinterpret_cast<const uint4*>(s_alw + cls * 16);
   const uint4 ma = m4[0], mb = m4[1], mc = m4[2], md = m4[3];
@@ -117,7 +119,8 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const uint32_t w3 = (c0 & v7) | (~c0 & v6);
   const uint32_t x0 = (c1 & w1) | (~c1 & w0);
   const uint32_t x1 = (c1 & w3) | (~c1 & w2);
-  const uint32_t alw = (c2 & x1) | (~c2 & x0);
+  alw = (c2 & x1) | (~c2 & x0);
+  }
 
   // transpose the planes (S, c0, c1, c2) into nibbles: nibble r of U[a] holds
   // the 4-bit table index S + 2*n of bit position 4r + a
@@ -147,10 +150,19 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
       const uint32_t Y2 = ((U[q] >> 2) & 0x3C3C3C3Cu) | clsb;
 #pragma unroll
       for (uint32_t i = 0; i < 4; i++) {
-        const uint32_t t = *reinterpret_cast<const uint32_t*>(tb + ((Y >> (8 * i)) & 0xFFu));
-        if (u[i] < t) lt |= 1u << (q + 8 * i);
-        const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + ((Y2 >> (8 * i)) & 0xFFu));
-        if (two && v[i] < t2) lt |= 1u << (q + 4 + 8 * i);
+        if (FAST) {
+          // table word thr - 1, or 0xFFFFFFFF for "always" (dE <= 0); films
+          // with a reachable thr = 0 entry take the exact branch below
+          const uint32_t lo = *reinterpret_cast<const uint32_t*>(tb + ((Y >> (8 * i)) & 0xFFu));
+          const uint32_t lo2 = *reinterpret_cast<const uint32_t*>(tb + ((Y2 >> (8 * i)) & 0xFFu));
+          if (u[i] <= lo) lt |= 1u << (q + 8 * i);
+          if (two && v[i] <= lo2) lt |= 1u << (q + 4 + 8 * i);
+        } else {
+          const uint32_t t = *reinterpret_cast<const uint32_t*>(tb + ((Y >> (8 * i)) & 0xFFu));
+          if (u[i] < t) lt |= 1u << (q + 8 * i);
+          const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + ((Y2 >> (8 * i)) & 0xFFu));
+          if (two && v[i] < t2) lt |= 1u << (q + 4 + 8 * i);
+        }
       }
     }
   }
@@ -174,10 +186,11 @@ __device__ __forceinline__ void item_word(const FilmCtx& c, uint32_t item, uint3
   kx = kxm1 + 1;
 }
 
+template <bool FAST>
 __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
                                                const uint32_t* s_alw) {
   const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
-  const uint32_t v = full ? decide_word<true>(c, f, s_thr, s_alw) : decide_word<false>(c, f, s_thr, s_alw);
+  const uint32_t v = full ? decide_word<true, FAST>(c, f, s_thr, s_alw) : decide_word<false, FAST>(c, f, s_thr, s_alw);
   store_word(c, f, v);
   // ky = 1 rows then update their wrap partner row (kx', Ly); its wrap
   // neighbour is the word just written, so it is fetched only now
@@ -185,7 +198,7 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
     const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
     Fetched g;
     fetch_word(c, kx2, c.Ly, f.w, g);
-    const uint32_t v2 = full ? decide_word<true>(c, g, s_thr, s_alw) : decide_word<false>(c, g, s_thr, s_alw);
+    const uint32_t v2 = full ? decide_word<true, FAST>(c, g, s_thr, s_alw) : decide_word<false, FAST>(c, g, s_thr, s_alw);
     store_word(c, g, v2);
   }
 }
@@ -202,6 +215,7 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
   static_assert(sizeof(FilmDesc) % 16 == 0, "descriptor copied as uint4");
   __shared__ __align__(16) FilmDesc s_d;
   __shared__ __align__(16) uint32_t s_alw[64];
+  __shared__ __align__(16) uint32_t s_lo[64];
   const uint32_t nvb = hdr->upd_blocks;
   const uint32_t per = (nvb + gridDim.x - 1) / gridDim.x;
   const uint32_t vb_end = min(nvb, (blockIdx.x + 1) * per);
@@ -218,8 +232,13 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
       const uint4* src = reinterpret_cast<const uint4*>(films + f);
       uint4* dst = reinterpret_cast<uint4*>(&s_d);
       for (uint32_t i = threadIdx.x; i < kDescWords / 4; i += blockDim.x) dst[i] = src[i];
-      for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x)
-        s_alw[i] = ((films[f].always[i >> 4] >> (i & 15)) & 1u) ? 0xFFFFFFFFu : 0u;
+      __syncthreads();
+      const bool fast = !s_d.has_never;
+      for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
+        const bool a = (s_d.always[i >> 4] >> (i & 15)) & 1u;
+        s_alw[i] = a ? 0xFFFFFFFFu : 0u;
+        s_lo[i] = fast ? (a ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
+      }
       __syncthreads();
       cur = f;
       have = false;
@@ -255,21 +274,26 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
         have = true;
       }
     }
-    if (mine) update_fetched(c, cw, &s_d.thr[0][0], s_alw);
+    if (mine) {
+      if (s_d.has_never) update_fetched<false>(c, cw, s_lo, s_alw);
+      else update_fetched<true>(c, cw, s_lo, s_alw);
+    }
   }
 }
 
 // Single-film half-sweep.  The descriptor is a __grid_constant__ kernel
 // parameter, so every per-film constant is read straight from the constant
 // bank; each thread updates kFilmItems words, kFilmThreads words apart.
+template <bool FAST>
 __global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
 update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
                    uint32_t sweep) {
   __shared__ __align__(16) uint32_t s_thr[64];
   __shared__ __align__(16) uint32_t s_alw[64];
   for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
-    s_thr[i] = d.thr[i >> 4][i & 15];
-    s_alw[i] = ((d.always[i >> 4] >> (i & 15)) & 1u) ? 0xFFFFFFFFu : 0u;
+    const bool a = (d.always[i >> 4] >> (i & 15)) & 1u;
+    s_thr[i] = FAST ? (a ? 0xFFFFFFFFu : d.thr[i >> 4][i & 15] - 1u) : d.thr[i >> 4][i & 15];
+    s_alw[i] = a ? 0xFFFFFFFFu : 0u;
   }
   __syncthreads();
   FilmCtx c;
@@ -294,7 +318,7 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   }
 #pragma unroll
   for (uint32_t it = 0; it < kFilmItems; it++)
-    if (mine[it]) update_fetched(c, fw[it], s_thr, s_alw);
+    if (mine[it]) update_fetched<FAST>(c, fw[it], s_thr, s_alw);
 }
 
 // ------------------------------------------------------------ measurement
@@ -516,7 +540,8 @@ cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colou
   const uint32_t per = kFilmThreads * kFilmItems;
   const uint32_t grid = (d.upd_items + per - 1) / per;
   if (grid == 0) return cudaSuccess;
-  update_film_kernel<<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
+  if (d.has_never) update_film_kernel<false><<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
+  else update_film_kernel<true><<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ def test_build_and_exports():
 
 
 def test_ptxas_report_has_no_spills():
+    """Every kernel of the library fits its registers (no local-memory spills)."""
     from paper_1411_5588_gb300 import build
     build.build()
     rep = open(os.path.join(build.BUILD, "ising_kernels.o.ptxas.txt")).read()
