@@ -24,6 +24,18 @@ __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
   return (a & b) | (c & (a ^ b));
 }
 
+// acc | bit when u <= t: one compare setting a predicate and one predicated OR.
+__device__ __forceinline__ void or_if_le(uint32_t& acc, uint32_t u, uint32_t t, uint32_t bit) {
+  asm("{\n\t.reg .pred p;\n\tsetp.le.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+      : "+r"(acc) : "r"(u), "r"(t), "r"(bit));
+}
+
+// acc | bit when u < t.
+__device__ __forceinline__ void or_if_lt(uint32_t& acc, uint32_t u, uint32_t t, uint32_t bit) {
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+      : "+r"(acc) : "r"(u), "r"(t), "r"(bit));
+}
+
 // Per-launch constants of one film, kept in registers.
 struct FilmCtx {
   uint32_t* plane0;
@@ -153,15 +165,15 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
         if (FAST) {
           // table word thr - 1, or 0xFFFFFFFF for "always" (dE <= 0); films
           // with a reachable thr = 0 entry take the exact branch below
-          const uint32_t lo = *reinterpret_cast<const uint32_t*>(tb + ((Y >> (8 * i)) & 0xFFu));
-          const uint32_t lo2 = *reinterpret_cast<const uint32_t*>(tb + ((Y2 >> (8 * i)) & 0xFFu));
-          if (u[i] <= lo) lt |= 1u << (q + 8 * i);
-          if (two && v[i] <= lo2) lt |= 1u << (q + 4 + 8 * i);
+          const uint32_t lo = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y, 0, 0x4440 + i));
+          const uint32_t lo2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y2, 0, 0x4440 + i));
+          or_if_le(lt, u[i], lo, 1u << (q + 8 * i));
+          if (two) or_if_le(lt, v[i], lo2, 1u << (q + 4 + 8 * i));
         } else {
-          const uint32_t t = *reinterpret_cast<const uint32_t*>(tb + ((Y >> (8 * i)) & 0xFFu));
-          if (u[i] < t) lt |= 1u << (q + 8 * i);
-          const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + ((Y2 >> (8 * i)) & 0xFFu));
-          if (two && v[i] < t2) lt |= 1u << (q + 4 + 8 * i);
+          const uint32_t t = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y, 0, 0x4440 + i));
+          const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y2, 0, 0x4440 + i));
+          or_if_lt(lt, u[i], t, 1u << (q + 8 * i));
+          if (two) or_if_lt(lt, v[i], t2, 1u << (q + 4 + 8 * i));
         }
       }
     }
