@@ -65,6 +65,10 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   d.x_pbc = x_mode == ISING_X_PBC ? 1u : 0u;
   d.key0 = (uint32_t)seed ^ (uint32_t)(seed >> 32);
   d.key1 = replica;
+  for (int r = 0; r < 10; r++) {
+    d.rk0[r] = d.key0 + (uint32_t)r * kWeyl0;
+    d.rk1[r] = d.key1 + (uint32_t)r * kWeyl1;
+  }
   d.upd_items = d.Lx * (d.Ly - 1) * d.W;
   d.meas_bpl = std::max<uint32_t>(1, (d.Ly * d.W + kMeasureItemsPerBlock - 1) / kMeasureItemsPerBlock);
   d.active = 1;
@@ -133,7 +137,7 @@ void FilmSet::layout(bool assign_part) {
     d.upd_block_begin = ub;
     d.meas_block_begin = mb;
     if (assign_part) d.part_off = po;
-    ub += (d.upd_items + kUpdateBlock - 1) / kUpdateBlock;
+    ub += (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
     mb += d.Lx * d.meas_bpl;
     po += part_len(d);
   }
@@ -163,7 +167,7 @@ int FilmSet::upload() {
   uint32_t* om = ou + hh.upd_blocks;
   for (size_t f = 0; f < nf; f++) {
     const FilmDesc& d = h[f];
-    const uint32_t nb = (d.upd_items + kUpdateBlock - 1) / kUpdateBlock;
+    const uint32_t nb = (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
     for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
     for (uint32_t b = 0; b < d.Lx * d.meas_bpl; b++) om[d.meas_block_begin + b] = (uint32_t)f;
   }
@@ -176,7 +180,7 @@ int FilmSet::upload() {
   return ISING_OK;
 }
 
-uint32_t FilmSet::upd_grid() const { return std::min<uint32_t>(hh.upd_blocks, upd_grid_max()); }
+uint32_t FilmSet::upd_grid() const { return hh.upd_blocks; }
 uint32_t FilmSet::meas_grid() const { return std::min<uint32_t>(hh.meas_blocks, meas_grid_max()); }
 uint32_t FilmSet::fin_grid() const { return std::min<uint32_t>(hh.n_films, (uint32_t)(2 * n_sm)); }
 
@@ -348,6 +352,7 @@ int ising_set_options(ising* h, int y_mode, int x_mode, double H, uint32_t repli
   d.y_mode = (uint32_t)y_mode;
   d.x_pbc = x_mode == ISING_X_PBC;
   d.key1 = replica;
+  for (int r = 0; r < 10; r++) d.rk1[r] = replica + (uint32_t)r * kWeyl1;
   build_tables(d, h->J, H, h->H1, h->T);
   h->dirty = true;
   return ISING_OK;

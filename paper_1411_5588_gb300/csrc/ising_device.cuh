@@ -57,6 +57,8 @@ struct FilmDesc {
   uint32_t always[4];          // bit (s + 2*n_aligned): accept without a draw
   uint32_t has_never;          // some reachable entry has dE > 0 and thr = 0
   uint32_t reserved;
+  uint32_t rk0[10], rk1[10];   // Philox round keys: key + r * Weyl constant
+  uint32_t reserved2[4];
 };
 
 // Division by a runtime constant d < 2^31 for numerators n < 2^31 (round-up
@@ -110,76 +112,64 @@ __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, 
 
 // Philox calls that share the row, sweep and parity words of the counter:
 // the first round and half of the second depend only on those, so they are
-// computed once per row and reused for the eight calls of a word.
+// computed once per row and reused for the calls of a word.  rk0/rk1 are the
+// round keys (key + r * Weyl constant, r = 0..9).
 struct PhiloxRow {
   uint32_t r1_hi1, r1_c3, r2_c0, r2_c1;
   uint32_t r1_x2;
-  uint32_t k0, k1;
-  __device__ __forceinline__ PhiloxRow(uint32_t row, uint32_t sweep, uint32_t parity, uint32_t key0,
-                                       uint32_t key1) {
-    k0 = key0;
-    k1 = key1;
+  const uint32_t* rk0;
+  const uint32_t* rk1;
+  __device__ __forceinline__ PhiloxRow(uint32_t row, uint32_t sweep, uint32_t parity, const uint32_t* k0,
+                                       const uint32_t* k1)
+      : rk0(k0), rk1(k1) {
     // round 1 with counter (row, c1, sweep, parity): words 1..3 of the result
     // do not depend on c1.
-    uint32_t lo0 = kPhiloxM0 * row, hi0 = mulhi(kPhiloxM0, row);
-    uint32_t lo1 = kPhiloxM1 * sweep, hi1 = mulhi(kPhiloxM1, sweep);
-    r1_hi1 = hi1;            // x0 = hi1 ^ c1 ^ k0
-    uint32_t x1 = lo1;
-    r1_x2 = hi0 ^ parity ^ key1;
-    r1_c3 = lo0;
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * row, p1 = (uint64_t)kPhiloxM1 * sweep;
+    r1_hi1 = (uint32_t)(p1 >> 32);  // x0 = hi1 ^ c1 ^ k0
+    const uint32_t x1 = (uint32_t)p1;
+    r1_x2 = (uint32_t)(p0 >> 32) ^ parity ^ rk1[0];
+    r1_c3 = (uint32_t)p0;
     // round 2: the products of x2 are c1-independent
-    uint32_t k0b = key0 + kWeyl0;
-    uint32_t lo1b = kPhiloxM1 * r1_x2, hi1b = mulhi(kPhiloxM1, r1_x2);
-    r2_c0 = hi1b ^ x1 ^ k0b;
-    r2_c1 = lo1b;
+    const uint64_t q1 = (uint64_t)kPhiloxM1 * r1_x2;
+    r2_c0 = (uint32_t)(q1 >> 32) ^ x1 ^ rk0[1];
+    r2_c1 = (uint32_t)q1;
+  }
+  // Full Philox4x32-10 output for counter word 1 = c1.
+  __device__ __forceinline__ void draw(uint32_t c1, uint32_t out[4]) const {
+    const uint32_t x0 = r1_hi1 ^ c1 ^ rk0[0];  // end of round 1 (x1 = lo1, x2 = r1_x2, x3 = r1_c3)
+    const uint64_t pp = (uint64_t)kPhiloxM0 * x0;
+    uint32_t c0 = r2_c0, c1w = r2_c1, c2 = (uint32_t)(pp >> 32) ^ r1_c3 ^ rk1[1], c3 = (uint32_t)pp;
+#pragma unroll
+    for (int r = 2; r < 10; r++) {
+      const uint64_t p0 = (uint64_t)kPhiloxM0 * c0, p1 = (uint64_t)kPhiloxM1 * c2;
+      c0 = (uint32_t)(p1 >> 32) ^ c1w ^ rk0[r];
+      c1w = (uint32_t)p1;
+      c2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+      c3 = (uint32_t)p0;
+    }
+    out[0] = c0; out[1] = c1w; out[2] = c2; out[3] = c3;
   }
   // Two Philox calls (counter words 1 = c1a and c1b) computed side by side.
   __device__ __forceinline__ void draw2(uint32_t c1a, uint32_t c1b, uint32_t oa[4], uint32_t ob[4]) const {
-    const uint32_t k1b = k1 + kWeyl1;
-    const uint32_t xa = r1_hi1 ^ c1a ^ k0, xb = r1_hi1 ^ c1b ^ k0;
+    const uint32_t xa = r1_hi1 ^ c1a ^ rk0[0], xb = r1_hi1 ^ c1b ^ rk0[0];
     const uint64_t pa = (uint64_t)kPhiloxM0 * xa, pb = (uint64_t)kPhiloxM0 * xb;
-    uint32_t a0 = r2_c0, a1 = r2_c1, a2 = (uint32_t)(pa >> 32) ^ r1_c3 ^ k1b, a3 = (uint32_t)pa;
-    uint32_t b0 = r2_c0, b1 = r2_c1, b2 = (uint32_t)(pb >> 32) ^ r1_c3 ^ k1b, b3 = (uint32_t)pb;
-    uint32_t kk0 = k0 + 2u * kWeyl0, kk1 = k1 + 2u * kWeyl1;
+    uint32_t a0 = r2_c0, a1 = r2_c1, a2 = (uint32_t)(pa >> 32) ^ r1_c3 ^ rk1[1], a3 = (uint32_t)pa;
+    uint32_t b0 = r2_c0, b1 = r2_c1, b2 = (uint32_t)(pb >> 32) ^ r1_c3 ^ rk1[1], b3 = (uint32_t)pb;
 #pragma unroll
     for (int r = 2; r < 10; r++) {
       const uint64_t pa0 = (uint64_t)kPhiloxM0 * a0, pa1 = (uint64_t)kPhiloxM1 * a2;
       const uint64_t pb0 = (uint64_t)kPhiloxM0 * b0, pb1 = (uint64_t)kPhiloxM1 * b2;
-      a0 = (uint32_t)(pa1 >> 32) ^ a1 ^ kk0;
+      a0 = (uint32_t)(pa1 >> 32) ^ a1 ^ rk0[r];
       a1 = (uint32_t)pa1;
-      a2 = (uint32_t)(pa0 >> 32) ^ a3 ^ kk1;
+      a2 = (uint32_t)(pa0 >> 32) ^ a3 ^ rk1[r];
       a3 = (uint32_t)pa0;
-      b0 = (uint32_t)(pb1 >> 32) ^ b1 ^ kk0;
+      b0 = (uint32_t)(pb1 >> 32) ^ b1 ^ rk0[r];
       b1 = (uint32_t)pb1;
-      b2 = (uint32_t)(pb0 >> 32) ^ b3 ^ kk1;
+      b2 = (uint32_t)(pb0 >> 32) ^ b3 ^ rk1[r];
       b3 = (uint32_t)pb0;
-      kk0 += kWeyl0;
-      kk1 += kWeyl1;
     }
     oa[0] = a0; oa[1] = a1; oa[2] = a2; oa[3] = a3;
     ob[0] = b0; ob[1] = b1; ob[2] = b2; ob[3] = b3;
-  }
-  // Full Philox4x32-10 output for counter word 1 = c1.
-  __device__ __forceinline__ void draw(uint32_t c1, uint32_t out[4]) const {
-    uint32_t x0 = r1_hi1 ^ c1 ^ k0;  // end of round 1 (x1 = lo1, x2 = r1_x2, x3 = r1_c3)
-    uint32_t k1b = k1 + kWeyl1;
-    const uint64_t pp = (uint64_t)kPhiloxM0 * x0;
-    const uint32_t lo0 = (uint32_t)pp, hi0 = (uint32_t)(pp >> 32);
-    uint32_t c0 = r2_c0, c1w = r2_c1, c2 = hi0 ^ r1_c3 ^ k1b, c3 = lo0;  // end of round 2
-    uint32_t kk0 = k0 + 2u * kWeyl0, kk1 = k1 + 2u * kWeyl1;
-#pragma unroll
-    for (int r = 2; r < 10; r++) {
-      const uint64_t p0 = (uint64_t)kPhiloxM0 * c0, p1 = (uint64_t)kPhiloxM1 * c2;
-      const uint32_t l0 = (uint32_t)p0, h0 = (uint32_t)(p0 >> 32);
-      const uint32_t l1 = (uint32_t)p1, h1 = (uint32_t)(p1 >> 32);
-      c0 = h1 ^ c1w ^ kk0;
-      c1w = l1;
-      c2 = h0 ^ c3 ^ kk1;
-      c3 = l0;
-      kk0 += kWeyl0;
-      kk1 += kWeyl1;
-    }
-    out[0] = c0; out[1] = c1w; out[2] = c2; out[3] = c3;
   }
 };
 

@@ -40,7 +40,9 @@ __device__ __forceinline__ void or_if_lt(uint32_t& acc, uint32_t u, uint32_t t, 
 struct FilmCtx {
   uint32_t* plane0;
   uint32_t* plane1;
-  uint32_t Lx, Ly, n, W, Wp, y_mode, x_pbc, key0, key1, last_mask, last_calls;
+  uint32_t Lx, Ly, n, W, Wp, y_mode, x_pbc, last_mask, last_calls;
+  const uint32_t* rk0;  // Philox round keys (constant bank or shared memory)
+  const uint32_t* rk1;
   uint32_t colour, sweep;
 };
 
@@ -149,7 +151,7 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const uint32_t ncalls = FULL ? 8u : c.last_calls;
   const uint32_t clsb = (cls * 64u) * 0x01010101u;  // byte offset of this class's table
   const char* tb = reinterpret_cast<const char*>(s_thr);
-  const PhiloxRow pr(row, c.sweep, X, c.key0, c.key1);
+  const PhiloxRow pr(row, c.sweep, X, c.rk0, c.rk1);
   uint32_t lt = 0;
   // calls q and q + 4 are drawn together (two independent Philox chains)
 #pragma unroll
@@ -217,10 +219,32 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
 
 }  // namespace
 
-// Persistent half-sweep: block b walks a contiguous run of virtual blocks
-// (128 words each) and, while the arithmetic of one word runs, already holds
-// the neighbour words of the next one.
-__global__ void __launch_bounds__(kUpdateBlock, kUpdateMinBlocks)
+// The words of one block of kItemsPerBlock consecutive words: each thread
+// fetches its kFilmItems words (kFilmThreads apart) before deciding any.
+template <bool FAST>
+__device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
+                                            uint32_t dwl, uint32_t dym, uint32_t dyl,
+                                            const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw) {
+  Fetched fw[kFilmItems];
+  bool mine[kFilmItems];
+#pragma unroll
+  for (uint32_t it = 0; it < kFilmItems; it++) {
+    const uint32_t item = first + threadIdx.x + it * kFilmThreads;
+    mine[it] = item < items;
+    if (mine[it]) {
+      uint32_t kx, ky, w;
+      item_word(c, item, dwm, dwl, dym, dyl, kx, ky, w);
+      fetch_word(c, kx, ky, w, fw[it]);
+    }
+  }
+#pragma unroll
+  for (uint32_t it = 0; it < kFilmItems; it++)
+    if (mine[it]) update_fetched<FAST>(c, fw[it], s_thr, s_alw);
+}
+
+// Half-sweep of every film of a launch: block b handles kItemsPerBlock words
+// of film owner[b], whose descriptor is staged in shared memory.
+__global__ void __launch_bounds__(kFilmThreads, kMultiMinBlocks)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k) {
   constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
@@ -229,73 +253,39 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
   __shared__ __align__(16) uint32_t s_alw[64];
   __shared__ __align__(16) uint32_t s_lo[64];
   const uint32_t nvb = hdr->upd_blocks;
-  const uint32_t per = (nvb + gridDim.x - 1) / gridDim.x;
-  const uint32_t vb_end = min(nvb, (blockIdx.x + 1) * per);
-  uint32_t cur = 0xFFFFFFFFu;
-  FilmCtx c;
-  uint32_t dwm = 0, dwl = 0, dym = 0, dyl = 0;
-  bool run = false;
-  Fetched nxt;
-  bool have = false;
-  for (uint32_t vb = blockIdx.x * per; vb < vb_end; vb++) {
+  for (uint32_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
     const uint32_t f = owner[vb];  // the same for every thread of the block
-    if (f != cur) {
-      __syncthreads();
-      const uint4* src = reinterpret_cast<const uint4*>(films + f);
-      uint4* dst = reinterpret_cast<uint4*>(&s_d);
-      for (uint32_t i = threadIdx.x; i < kDescWords / 4; i += blockDim.x) dst[i] = src[i];
-      __syncthreads();
-      const bool fast = !s_d.has_never;
-      for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
-        const bool a = (s_d.always[i >> 4] >> (i & 15)) & 1u;
-        s_alw[i] = a ? 0xFFFFFFFFu : 0u;
-        s_lo[i] = fast ? (a ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
-      }
-      __syncthreads();
-      cur = f;
-      have = false;
-      run = s_d.active && s_d.sweep + k < s_d.sweep_end;
-      c.Lx = s_d.Lx; c.Ly = s_d.Ly; c.n = s_d.n; c.W = s_d.W; c.Wp = s_d.Wp;
-      c.y_mode = s_d.y_mode; c.x_pbc = s_d.x_pbc; c.key0 = s_d.key0; c.key1 = s_d.key1;
-      c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
-      c.colour = colour; c.sweep = s_d.sweep + k;
-      c.plane0 = pool + s_d.spin_off;
-      c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
-      dwm = s_d.divw_m; dwl = s_d.divw_l; dym = s_d.divy_m; dyl = s_d.divy_l;
+    __syncthreads();
+    const uint4* src = reinterpret_cast<const uint4*>(films + f);
+    uint4* dst = reinterpret_cast<uint4*>(&s_d);
+    for (uint32_t i = threadIdx.x; i < kDescWords / 4; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    const bool fast = !s_d.has_never;
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
+      const bool a = (s_d.always[i >> 4] >> (i & 15)) & 1u;
+      s_alw[i] = a ? 0xFFFFFFFFu : 0u;
+      s_lo[i] = fast ? (a ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
     }
-    if (!run) continue;
-    const uint32_t first = s_d.upd_block_begin, items = s_d.upd_items;
-    const uint32_t item = (vb - first) * kUpdateBlock + threadIdx.x;
-    Fetched cw;
-    const bool mine = item < items;
-    if (have) {
-      cw = nxt;
-    } else if (mine) {
-      uint32_t kx, ky, w;
-      item_word(c, item, dwm, dwl, dym, dyl, kx, ky, w);
-      fetch_word(c, kx, ky, w, cw);
-    }
-    // fetch the next virtual block's word now if it belongs to the same film
-    have = false;
-    if (vb + 1 < vb_end && owner[vb + 1] == f) {
-      const uint32_t item2 = item + kUpdateBlock;
-      if (item2 < items) {
-        uint32_t kx, ky, w;
-        item_word(c, item2, dwm, dwl, dym, dyl, kx, ky, w);
-        fetch_word(c, kx, ky, w, nxt);
-        have = true;
-      }
-    }
-    if (mine) {
-      if (s_d.has_never) update_fetched<false>(c, cw, s_lo, s_alw);
-      else update_fetched<true>(c, cw, s_lo, s_alw);
-    }
+    __syncthreads();
+    if (!s_d.active || s_d.sweep + k >= s_d.sweep_end) continue;
+    FilmCtx c;
+    c.Lx = s_d.Lx; c.Ly = s_d.Ly; c.n = s_d.n; c.W = s_d.W; c.Wp = s_d.Wp;
+    c.y_mode = s_d.y_mode; c.x_pbc = s_d.x_pbc; c.rk0 = s_d.rk0; c.rk1 = s_d.rk1;
+    c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
+    c.colour = colour; c.sweep = s_d.sweep + k;
+    c.plane0 = pool + s_d.spin_off;
+    c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
+    const uint32_t first = (vb - s_d.upd_block_begin) * kItemsPerBlock;
+    if (fast)
+      sweep_block<true>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
+    else
+      sweep_block<false>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
   }
 }
 
 // Single-film half-sweep.  The descriptor is a __grid_constant__ kernel
-// parameter, so every per-film constant is read straight from the constant
-// bank; each thread updates kFilmItems words, kFilmThreads words apart.
+// parameter, so every per-film constant (round keys included) is read straight
+// from the constant bank; block b updates words b*kItemsPerBlock onwards.
 template <bool FAST>
 __global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
 update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
@@ -310,27 +300,13 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   __syncthreads();
   FilmCtx c;
   c.Lx = d.Lx; c.Ly = d.Ly; c.n = d.n; c.W = d.W; c.Wp = d.Wp;
-  c.y_mode = d.y_mode; c.x_pbc = d.x_pbc; c.key0 = d.key0; c.key1 = d.key1;
+  c.y_mode = d.y_mode; c.x_pbc = d.x_pbc; c.rk0 = d.rk0; c.rk1 = d.rk1;
   c.last_mask = d.last_mask; c.last_calls = d.last_calls;
   c.colour = colour; c.sweep = sweep;
   c.plane0 = pool + d.spin_off;
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
-  const uint32_t base = blockIdx.x * (kFilmThreads * kFilmItems) + threadIdx.x;
-  Fetched fw[kFilmItems];
-  bool mine[kFilmItems];
-#pragma unroll
-  for (uint32_t it = 0; it < kFilmItems; it++) {
-    const uint32_t item = base + it * kFilmThreads;
-    mine[it] = item < d.upd_items;
-    if (mine[it]) {
-      uint32_t kx, ky, w;
-      item_word(c, item, d.divw_m, d.divw_l, d.divy_m, d.divy_l, kx, ky, w);
-      fetch_word(c, kx, ky, w, fw[it]);
-    }
-  }
-#pragma unroll
-  for (uint32_t it = 0; it < kFilmItems; it++)
-    if (mine[it]) update_fetched<FAST>(c, fw[it], s_thr, s_alw);
+  sweep_block<FAST>(c, blockIdx.x * kItemsPerBlock, d.upd_items, d.divw_m, d.divw_l, d.divy_m, d.divy_l, s_thr,
+                    s_alw);
 }
 
 // ------------------------------------------------------------ measurement
@@ -543,14 +519,13 @@ __global__ void unpack_kernel(FilmDesc F, const uint32_t* __restrict__ pool, int
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k,
                           cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  update_kernel<<<grid, kUpdateBlock, 0, st>>>(L.films, L.owner_upd, L.hdr, pool, colour, k);
+  update_kernel<<<grid, kFilmThreads, 0, st>>>(L.films, L.owner_upd, L.hdr, pool, colour, k);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep,
                                cudaStream_t st) {
-  const uint32_t per = kFilmThreads * kFilmItems;
-  const uint32_t grid = (d.upd_items + per - 1) / per;
+  const uint32_t grid = (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
   if (grid == 0) return cudaSuccess;
   if (d.has_never) update_film_kernel<false><<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
   else update_film_kernel<true><<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
@@ -595,7 +570,7 @@ cudaError_t launch_unpack(const FilmDesc& f, const uint32_t* pool, int8_t* s, cu
 
 int update_blocks_per_sm() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel, kUpdateBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel, kFilmThreads, 0) != cudaSuccess) return 0;
   return nb;
 }
 

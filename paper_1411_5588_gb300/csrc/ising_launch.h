@@ -8,13 +8,13 @@
 
 namespace isg {
 
-constexpr int kUpdateBlock = 128;
-constexpr int kUpdateMinBlocks = 5;
-
-// Single-film kernel: threads per block, words per thread, blocks per SM.
+// Update kernels: threads per block, words per thread, blocks per SM; one
+// block updates kItemsPerBlock consecutive words of one film.
 constexpr uint32_t kFilmThreads = 128;
 constexpr uint32_t kFilmItems = 2;
 constexpr int kFilmMinBlocks = 6;
+constexpr int kMultiMinBlocks = 5;  // the multi-film kernel carries both table paths
+constexpr uint32_t kItemsPerBlock = kFilmThreads * kFilmItems;
 constexpr int kMeasureBlock = 256;
 
 // Items a measurement block covers per layer before another block is added.
