@@ -441,8 +441,8 @@ measure_finalize_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restric
 }
 
 __global__ void advance_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restrict__ hdr, uint32_t n_sweeps) {
-  const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f < hdr->n_films && films[f].active) {
+  for (uint32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < hdr->n_films; f += gridDim.x * blockDim.x) {
+    if (!films[f].active) continue;
     const uint32_t s = films[f].sweep, e = films[f].sweep_end;
     films[f].sweep = (e - s < n_sweeps) ? e : s + n_sweeps;
   }

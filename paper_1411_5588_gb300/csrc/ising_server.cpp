@@ -1,13 +1,22 @@
 // Continuous-batching job server.
 //
 // Jobs (film shape, T, H1, key, sweeps) are queued by ising_batch_submit.  A
-// host thread repeatedly (1) admits queued jobs whose packed lattice, record
-// series, partial sums and unpack staging fit in a device arena of fixed size,
-// (2) runs one chunk of sweeps over every admitted job in shared launches --
-// a job that reaches its last sweep inside a chunk simply stops (sweep_end),
-// (3) retires finished jobs, copying their records and final spins to the
-// host and returning their arena space.  Each job's random stream depends only
-// on its own key, so its result is the same alone or in any mix.
+// host thread keeps the device busy with chunks of `chunk` sweeps over every
+// admitted job, two chunks in flight:
+//   1. before reusing a slot (one of two), wait for the chunk that last used
+//      it and retire the jobs that finished in it: copy their records and
+//      final spins out of pinned staging, return their arena space;
+//   2. admit queued jobs, in arrival order, while their packed lattice, record
+//      series, partial sums and unpack staging fit in a fixed device arena;
+//   3. write the descriptors of the running jobs into the slot's pinned
+//      staging, copy them to the slot's device buffer, enqueue the chunk's
+//      update/measure launches over all of them and an advance of their sweep
+//      counters, and queue the unpack + copy-out of the jobs that finish
+//      inside the chunk.
+// The host prepares chunk i+1 while chunk i runs.
+// A job that reaches its last sweep inside a chunk stops there (sweep_end).
+// Each job's random stream depends only on its own key, so its result is the
+// same alone or in any mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +38,7 @@ using namespace isg;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr double kWaitLimit = 600.0;  // seconds a chunk may take before the server gives up
 
 // First-fit allocator over [0, size) bytes.
 struct Arena {
@@ -79,7 +89,7 @@ struct Job {
   ising_job p{};
   JobState state = kQueued;
   double t_submit = 0, t_admit = 0, t_finish = 0;
-  FilmDesc d{};
+  FilmDesc d{};  // host mirror; d.sweep = sweeps enqueued so far
   uint64_t n_records = 0;
   size_t off_spin = 0, off_rec = 0, off_part = 0, off_stage = 0;
   size_t b_spin = 0, b_rec = 0, b_part = 0, b_stage = 0;
@@ -89,6 +99,30 @@ struct Job {
 };
 
 size_t round_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+void job_footprint(Job& j) {
+  const FilmDesc& d = j.d;
+  j.b_spin = round_up(film_words(d) * sizeof(uint32_t));
+  j.b_rec = round_up(std::max<uint64_t>(j.n_records, 1) * record_len(d) * sizeof(int64_t));
+  j.b_part = round_up(part_len(d) * sizeof(int64_t));
+  j.b_stage = round_up((size_t)d.Lx * d.Ly * d.Lz);
+}
+
+size_t footprint_bytes(const Job& j) { return j.b_spin + j.b_rec + j.b_part + j.b_stage; }
+
+// One of the two chunk slots: device descriptors, pinned staging for them, the
+// event that marks the chunk done, and pinned space for finished results.
+struct Slot {
+  char* d_meta = nullptr;
+  char* h_stage = nullptr;
+  cudaEvent_t done = nullptr;
+  LaunchSet L;
+  bool busy = false;
+  std::vector<ising_ticket> finishing;
+  std::vector<size_t> res_off;
+  char* h_res = nullptr;
+  size_t res_cap = 0;
+};
 
 }  // namespace
 
@@ -103,7 +137,7 @@ struct ising_server {
   uint32_t chunk = 100;
   char* arena_dev = nullptr;
   Arena arena;
-  FilmSet fs;
+  FilmSet fs;  // device, stream, occupancy; pool/part/rec point into the arena
   std::deque<ising_ticket> queue;
   std::unordered_map<ising_ticket, Job> jobs;
   std::vector<ising_ticket> running;
@@ -111,116 +145,113 @@ struct ising_server {
   uint64_t n_finished = 0, n_chunks = 0, attempts = 0;
   std::chrono::steady_clock::time_point t0;
 
+  // chunk slots and the capacities their descriptor buffers were sized for
+  Slot slot[2];
+  uint32_t cap_films = 0, cap_upd = 0, cap_meas = 0;
+  size_t meta_bytes = 0;
+  uint32_t grid_upd = 0, grid_meas = 0, grid_fin = 0, grid_adv = 0;
+
   double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
   void loop();
-  int run_chunk(std::unique_lock<std::mutex>& lk);
+  int ensure_capacity(uint32_t nf, uint32_t nu, uint32_t nm);
+  int wait_slot(Slot& s);
+  void retire(Slot& s);  // with the lock held
+  void release_slots();
 };
 
-namespace {
-
-void job_footprint(Job& j) {
-  const FilmDesc& d = j.d;
-  j.b_spin = round_up(film_words(d) * sizeof(uint32_t));
-  j.b_rec = round_up(std::max<uint64_t>(j.n_records, 1) * record_len(d) * sizeof(int64_t));
-  j.b_part = round_up(part_len(d) * sizeof(int64_t));
-  j.b_stage = round_up((size_t)d.Lx * d.Ly * d.Lz);
+// Descriptor buffers large enough for nf films, nu update and nm measurement
+// blocks (grown only between chunks, once no chunk uses them).
+int ising_server::ensure_capacity(uint32_t nf, uint32_t nu, uint32_t nm) {
+  if (nf <= cap_films && nu <= cap_upd && nm <= cap_meas && slot[0].d_meta) return ISING_OK;
+  for (Slot& s : slot) {
+    int rc = wait_slot(s);
+    if (rc) return rc;
+  }
+  auto grow = [](uint32_t cap, uint32_t need, uint32_t floor_) {
+    if (cap >= need && cap >= floor_) return cap;
+    return std::max<uint32_t>({floor_, need, 2 * cap});
+  };
+  cap_films = grow(cap_films, nf, 1024);
+  cap_upd = grow(cap_upd, nu, 1u << 16);
+  cap_meas = grow(cap_meas, nm, 1u << 16);
+  meta_bytes = sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc) + ((size_t)cap_upd + cap_meas) * 4;
+  for (Slot& s : slot) {
+    if (s.d_meta) cudaFree(s.d_meta);
+    if (s.h_stage) cudaFreeHost(s.h_stage);
+    s.d_meta = nullptr;
+    s.h_stage = nullptr;
+    ISG_CK(cudaMalloc(&s.d_meta, meta_bytes));
+    ISG_CK(cudaMallocHost(&s.h_stage, meta_bytes));
+    s.L.hdr = reinterpret_cast<LaunchHdr*>(s.d_meta);
+    s.L.films = reinterpret_cast<FilmDesc*>(s.d_meta + sizeof(LaunchHdr));
+    s.L.owner_upd = reinterpret_cast<uint32_t*>(s.d_meta + sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc));
+    s.L.owner_meas = s.L.owner_upd + cap_upd;
+  }
+  return ISING_OK;
 }
 
-size_t footprint_bytes(const Job& j) { return j.b_spin + j.b_rec + j.b_part + j.b_stage; }
+int ising_server::wait_slot(Slot& s) {
+  if (!s.busy) return ISING_OK;
+  const auto t = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(s.done);
+    if (e == cudaSuccess) return ISING_OK;
+    if (e != cudaErrorNotReady) return fail(ISING_ECUDA, "chunk: %s", cudaGetErrorString(e));
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count() > kWaitLimit)
+      return fail(ISING_ETIMEOUT, "a chunk ran longer than %.0f s", kWaitLimit);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
 
-}  // namespace
-
-// Runs one chunk over the running jobs; called with the lock held, releases it
-// while the device works.
-int ising_server::run_chunk(std::unique_lock<std::mutex>& lk) {
-  // descriptors of the running jobs
-  fs.h.clear();
-  std::vector<ising_ticket> films = running;
-  for (ising_ticket t : films) fs.h.push_back(jobs[t].d);
-  std::vector<Job*> fresh;
-  for (ising_ticket t : films)
-    if (!jobs[t].inited) fresh.push_back(&jobs[t]);
-  lk.unlock();
-  fs.layout(false);  // partial sums stay in each job's own arena area
-  for (Job* j : fresh) {
-    uint32_t flip_lo = 0;
-    int flip_all = 0;
-    if (j->p.init_kind == ISING_INIT_SLAB_Y) {
-      const double t = std::floor(std::ldexp(j->p.flip_p, 32));
-      if (t >= 4294967296.0) flip_all = 1; else flip_lo = (uint32_t)t;
-    }
-    ISG_CK(launch_init(j->d, fs.pool, j->p.init_kind, flip_lo, flip_all, fs.stream));
-  }
-  int rc = fs.upload();
-  if (rc) return rc;
-  uint32_t K = chunk;
-  uint64_t work = 0;
-  for (const auto& d : fs.h) {
-    const uint32_t left = d.sweep_end - d.sweep;
-    work += (uint64_t)std::min(left, K) * d.Lx * d.Ly * d.Lz;
-  }
-  rc = fs.enqueue_sweeps(0, K, false, false);
-  if (rc) return rc;
-  ISG_CK(launch_advance(fs.L, (fs.hh.n_films + 127) / 128, K, fs.stream));
-  // finished jobs: final spins into their staging areas
-  std::vector<size_t> done_idx;
-  for (size_t f = 0; f < fs.h.size(); f++) {
-    FilmDesc& d = fs.h[f];
-    const uint32_t left = d.sweep_end - d.sweep;
-    d.sweep = left <= K ? d.sweep_end : d.sweep + K;
-    if (d.measure_every) d.rec_next = d.sweep / d.measure_every;
-    if (d.sweep == d.sweep_end) {
-      done_idx.push_back(f);
-      Job* j = nullptr;
-      {
-        lk.lock();
-        j = &jobs[films[f]];
-        lk.unlock();
-      }
-      ISG_CK(launch_unpack(d, fs.pool, reinterpret_cast<int8_t*>(arena_dev + j->off_stage), fs.stream));
-    }
-  }
-  rc = wait_stream(fs.stream, 600.0);
-  if (rc) return rc;
-  std::vector<std::pair<ising_ticket, Job*>> fin;
-  lk.lock();
-  for (ising_ticket t : films) jobs[t].inited = true;
-  for (size_t f = 0; f < fs.h.size(); f++) jobs[films[f]].d = fs.h[f];
-  for (size_t f : done_idx) fin.push_back({films[f], &jobs[films[f]]});
-  n_chunks++;
-  attempts += work;
-  lk.unlock();
-  for (auto& pr : fin) {
-    Job* j = pr.second;
-    const size_t rl = record_len(j->d);
-    j->records.resize(j->n_records * rl);
-    if (j->n_records)
-      ISG_CK(cudaMemcpy(j->records.data(), arena_dev + j->off_rec, j->n_records * rl * sizeof(int64_t),
-                        cudaMemcpyDeviceToHost));
-    j->spins.resize((size_t)j->d.Lx * j->d.Ly * j->d.Lz);
-    ISG_CK(cudaMemcpy(j->spins.data(), arena_dev + j->off_stage, j->spins.size(), cudaMemcpyDeviceToHost));
-  }
-  lk.lock();
+void ising_server::retire(Slot& s) {
   const double tf = now();
-  for (auto& pr : fin) {
-    Job* j = pr.second;
-    arena.release(j->off_spin, j->b_spin);
-    arena.release(j->off_rec, j->b_rec);
-    arena.release(j->off_part, j->b_part);
-    arena.release(j->off_stage, j->b_stage);
-    j->state = kDone;
-    j->t_finish = tf;
+  for (size_t i = 0; i < s.finishing.size(); i++) {
+    Job& j = jobs[s.finishing[i]];
+    const size_t rl = record_len(j.d);
+    const size_t rb = j.n_records * rl * sizeof(int64_t);
+    j.records.resize(j.n_records * rl);
+    if (rb) std::memcpy(j.records.data(), s.h_res + s.res_off[i], rb);
+    j.spins.resize((size_t)j.d.Lx * j.d.Ly * j.d.Lz);
+    std::memcpy(j.spins.data(), s.h_res + s.res_off[i] + rb, j.spins.size());
+    arena.release(j.off_spin, j.b_spin);
+    arena.release(j.off_rec, j.b_rec);
+    arena.release(j.off_part, j.b_part);
+    arena.release(j.off_stage, j.b_stage);
+    j.state = kDone;
+    j.t_finish = tf;
     n_finished++;
-    running.erase(std::find(running.begin(), running.end(), pr.first));
   }
-  if (!fin.empty()) cv_done.notify_all();
-  return ISING_OK;
+  if (!s.finishing.empty()) {
+    running.erase(std::remove_if(running.begin(), running.end(),
+                                 [&](ising_ticket t) { return jobs[t].state == kDone; }),
+                  running.end());
+    cv_done.notify_all();
+  }
+  s.finishing.clear();
+  s.res_off.clear();
+  s.busy = false;
 }
 
 void ising_server::loop() {
   cudaSetDevice(fs.device);
   std::unique_lock<std::mutex> lk(mu);
+  uint64_t chunk_id = 0;
+  auto stop_with = [&](int rc) {
+    error = rc;
+    error_msg = last_error();
+    stop = true;
+    cv_done.notify_all();
+  };
   while (!stop) {
+    Slot& S = slot[chunk_id % 2];
+    Slot& O = slot[(chunk_id + 1) % 2];
+    if (S.busy) {
+      lk.unlock();
+      const int rc = wait_slot(S);
+      lk.lock();
+      if (rc) { stop_with(rc); break; }
+      retire(S);
+    }
     // admission in arrival order while the arena has room
     while (!queue.empty()) {
       Job& j = jobs[queue.front()];
@@ -241,18 +272,135 @@ void ising_server::loop() {
       running.push_back(queue.front());
       queue.pop_front();
     }
-    if (running.empty()) {
-      cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    // jobs with sweeps left to enqueue
+    std::vector<ising_ticket> films;
+    for (ising_ticket t : running)
+      if (jobs[t].d.sweep < jobs[t].d.sweep_end) films.push_back(t);
+    if (films.empty()) {
+      if (O.busy) {  // let the other chunk finish and retire it
+        lk.unlock();
+        const int rc = wait_slot(O);
+        lk.lock();
+        if (rc) { stop_with(rc); break; }
+        retire(O);
+        continue;
+      }
+      cv_work.wait_for(lk, std::chrono::milliseconds(2));
       continue;
     }
-    int rc = run_chunk(lk);
-    if (!lk.owns_lock()) lk.lock();
-    if (rc) {
-      error = rc;
-      error_msg = last_error();
-      stop = true;
-      cv_done.notify_all();
+    // descriptors, owner tables and the jobs finishing in this chunk
+    fs.h.clear();
+    std::vector<Job*> fresh, fin;
+    for (ising_ticket t : films) {
+      Job& j = jobs[t];
+      fs.h.push_back(j.d);
+      if (!j.inited) fresh.push_back(&j);
+      if (j.d.sweep_end - j.d.sweep <= chunk) fin.push_back(&j);
     }
+    S.finishing.clear();
+    for (ising_ticket t : films)
+      if (jobs[t].d.sweep_end - jobs[t].d.sweep <= chunk) S.finishing.push_back(t);
+    lk.unlock();
+    fs.layout(false);  // partial sums stay in each job's own arena area
+    int rc = ensure_capacity(fs.hh.n_films, fs.hh.upd_blocks, fs.hh.meas_blocks);
+    if (!rc) {
+      char* p = S.h_stage;
+      std::memcpy(p, &fs.hh, sizeof fs.hh);
+      std::memcpy(p + sizeof(LaunchHdr), fs.h.data(), fs.h.size() * sizeof(FilmDesc));
+      uint32_t* ou = reinterpret_cast<uint32_t*>(p + sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc));
+      uint32_t* om = ou + cap_upd;
+      for (size_t f = 0; f < fs.h.size(); f++) {
+        const FilmDesc& d = fs.h[f];
+        const uint32_t nb = (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
+        for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
+        for (uint32_t b = 0; b < d.Lx * d.meas_bpl; b++) om[d.meas_block_begin + b] = (uint32_t)f;
+      }
+      // pinned space for the results of the jobs finishing in this chunk
+      size_t need = 0;
+      S.res_off.clear();
+      for (Job* j : fin) {
+        S.res_off.push_back(need);
+        need += j->n_records * record_len(j->d) * sizeof(int64_t) + (size_t)j->d.Lx * j->d.Ly * j->d.Lz;
+        need = (need + 15) / 16 * 16;
+      }
+      if (need > S.res_cap) {
+        if (S.h_res) cudaFreeHost(S.h_res);
+        S.h_res = nullptr;
+        S.res_cap = std::max(need, 2 * S.res_cap);
+        if (cudaMallocHost(&S.h_res, S.res_cap) != cudaSuccess) {
+          S.res_cap = 0;
+          rc = fail(ISING_ENOMEM, "cannot allocate %zu bytes of pinned result staging", need);
+        }
+      }
+    }
+    for (Job* j : fresh) {
+      if (rc) break;
+      uint32_t flip_lo = 0;
+      int flip_all = 0;
+      if (j->p.init_kind == ISING_INIT_SLAB_Y) {
+        const double t = std::floor(std::ldexp(j->p.flip_p, 32));
+        if (t >= 4294967296.0) flip_all = 1; else flip_lo = (uint32_t)t;
+      }
+      if (launch_init(j->d, fs.pool, j->p.init_kind, flip_lo, flip_all, fs.stream) != cudaSuccess)
+        rc = fail(ISING_ECUDA, "init launch failed");
+    }
+    if (!rc) {  // the used parts of [hdr | films | owner_upd | owner_meas]
+      const size_t off_u = sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc);
+      const size_t off_m = off_u + (size_t)cap_upd * 4;
+      const size_t b0 = sizeof(LaunchHdr) + fs.h.size() * sizeof(FilmDesc);
+      if (cudaMemcpyAsync(S.d_meta, S.h_stage, b0, cudaMemcpyHostToDevice, fs.stream) != cudaSuccess ||
+          cudaMemcpyAsync(S.d_meta + off_u, S.h_stage + off_u, (size_t)fs.hh.upd_blocks * 4,
+                          cudaMemcpyHostToDevice, fs.stream) != cudaSuccess ||
+          cudaMemcpyAsync(S.d_meta + off_m, S.h_stage + off_m, (size_t)fs.hh.meas_blocks * 4,
+                          cudaMemcpyHostToDevice, fs.stream) != cudaSuccess)
+        rc = fail(ISING_ECUDA, "descriptor upload failed");
+    }
+    if (!rc) {  // the chunk: exact grids, records only after sweeps where some job takes one
+      fs.L = S.L;
+      rc = fs.enqueue_sweeps(0, chunk, false, false);
+      if (!rc && launch_advance(S.L, grid_adv, chunk, fs.stream) != cudaSuccess)
+        rc = fail(ISING_ECUDA, "advance launch failed");
+    }
+    for (size_t i = 0; !rc && i < fin.size(); i++) {
+      Job* j = fin[i];
+      FilmDesc d = j->d;  // geometry and offsets of the finished film
+      const size_t rb = j->n_records * record_len(d) * sizeof(int64_t);
+      if (rb && cudaMemcpyAsync(S.h_res + S.res_off[i], arena_dev + j->off_rec, rb, cudaMemcpyDeviceToHost,
+                                fs.stream) != cudaSuccess)
+        rc = fail(ISING_ECUDA, "record copy-out failed");
+      if (!rc && launch_unpack(d, fs.pool, reinterpret_cast<int8_t*>(arena_dev + j->off_stage), fs.stream) !=
+                     cudaSuccess)
+        rc = fail(ISING_ECUDA, "unpack launch failed");
+      if (!rc && cudaMemcpyAsync(S.h_res + S.res_off[i] + rb, arena_dev + j->off_stage,
+                                 (size_t)d.Lx * d.Ly * d.Lz, cudaMemcpyDeviceToHost, fs.stream) != cudaSuccess)
+        rc = fail(ISING_ECUDA, "spin copy-out failed");
+    }
+    if (!rc && cudaEventRecord(S.done, fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
+    lk.lock();
+    if (rc) { stop_with(rc); break; }
+    uint64_t work = 0;
+    for (ising_ticket t : films) {
+      Job& j = jobs[t];
+      j.inited = true;
+      const uint32_t left = j.d.sweep_end - j.d.sweep;
+      work += (uint64_t)std::min(left, chunk) * j.d.Lx * j.d.Ly * j.d.Lz;
+      j.d.sweep = left <= chunk ? j.d.sweep_end : j.d.sweep + chunk;
+      if (j.d.measure_every) j.d.rec_next = j.d.sweep / j.d.measure_every;
+    }
+    S.busy = true;
+    n_chunks++;
+    attempts += work;
+    chunk_id++;
+  }
+}
+
+void ising_server::release_slots() {
+  for (Slot& s : slot) {
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.d_meta) cudaFree(s.d_meta);
+    if (s.h_stage) cudaFreeHost(s.h_stage);
+    if (s.h_res) cudaFreeHost(s.h_res);
+    s = Slot();
   }
 }
 
@@ -263,7 +411,7 @@ int ising_server_create(size_t hbm_budget_bytes, uint32_t chunk_sweeps, ising_se
   if (!out) return fail(ISING_EINVAL, "out is NULL");
   *out = nullptr;
   if (hbm_budget_bytes < (1u << 20)) return fail(ISING_EINVAL, "budget must be at least 1 MiB");
-  if (chunk_sweeps == 0) return fail(ISING_EINVAL, "chunk_sweeps must be > 0");
+  if (chunk_sweeps == 0 || chunk_sweeps > 4096) return fail(ISING_EINVAL, "chunk_sweeps must be in 1..4096");
   ising_server* s = new (std::nothrow) ising_server();
   if (!s) return fail(ISING_ENOMEM, "host allocation failed");
   s->budget = hbm_budget_bytes / kAlign * kAlign;
@@ -280,6 +428,22 @@ int ising_server_create(size_t hbm_budget_bytes, uint32_t chunk_sweeps, ising_se
   s->fs.pool = reinterpret_cast<uint32_t*>(s->arena_dev);
   s->fs.rec = reinterpret_cast<int64_t*>(s->arena_dev);
   s->fs.part = reinterpret_cast<int64_t*>(s->arena_dev);
+  s->grid_upd = s->fs.upd_grid_max();
+  s->grid_meas = s->fs.meas_grid_max();
+  s->grid_fin = (uint32_t)(2 * s->fs.n_sm);
+  s->grid_adv = 64;
+  for (Slot& sl : s->slot)
+    if (!rc && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+      rc = fail(ISING_ECUDA, "event creation failed");
+  if (!rc) rc = s->ensure_capacity(1, 1, 1);
+  if (rc) {
+    s->release_slots();
+    cudaFree(s->arena_dev);
+    s->fs.pool = nullptr; s->fs.rec = nullptr; s->fs.part = nullptr;
+    s->fs.release();
+    delete s;
+    return rc;
+  }
   s->t0 = std::chrono::steady_clock::now();
   s->worker = std::thread([s] { s->loop(); });
   *out = s;
@@ -377,6 +541,7 @@ int ising_batch_result(ising_server* s, ising_ticket t, int64_t* buf, size_t cap
     info->t_finish = j.t_finish;
     info->n_records = j.n_records;
   }
+  s->running.erase(std::remove(s->running.begin(), s->running.end(), t), s->running.end());
   s->jobs.erase(it);
   return ISING_OK;
 }
@@ -388,7 +553,10 @@ int ising_server_get_stats(ising_server* s, ising_server_stats* st) {
   st->bytes_in_use = s->arena.used;
   st->bytes_budget = s->budget;
   st->queued = s->queue.size();
-  st->running = s->running.size();
+  uint64_t run = 0;
+  for (ising_ticket t : s->running)
+    if (s->jobs.count(t) && s->jobs[t].state == kRunning) run++;
+  st->running = run;
   st->finished = s->n_finished;
   st->chunks = s->n_chunks;
   st->attempts = s->attempts;
@@ -404,6 +572,7 @@ int ising_server_destroy(ising_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   if (s->fs.stream) cudaStreamSynchronize(s->fs.stream);
+  s->release_slots();
   s->fs.pool = nullptr;
   s->fs.rec = nullptr;
   s->fs.part = nullptr;
