@@ -256,6 +256,66 @@ def serving(ig, WL, n_jobs=2000, chunk=50, budget=16 << 30):
             "chunk_sweeps": chunk, "chunks": st["chunks"]}
 
 
+def serving_capacity(ig, WL, n_jobs=400, n_plain=40, chunk=50, budget=16 << 30):
+    """Saturated server (the first n_jobs of the stream submitted at once)
+    against the same kind of jobs run one after another through the
+    single-film path (the first n_plain of them)."""
+    jobs = WL.serve_2000()[:n_jobs]
+    srv = ig.Server(budget, chunk_sweeps=chunk)
+    t0 = time.perf_counter()
+    tickets = srv.submit(jobs)
+    for t in tickets:
+        srv.wait(t, 3600.0)
+        srv.result(t, want_spins=False)
+    served = sum(WL.sites(j) * j["n_sweeps"] for j in jobs) / (time.perf_counter() - t0) / 1e9
+    srv.close()
+    att = 0
+    t0 = time.perf_counter()
+    for j in jobs[:n_plain]:
+        g = ig.Film(j["Lx"], j["Ly"], j["Lz"], j["J"], j["H1"], j["T"], j["seed"], replica=j["replica"])
+        g.init(j["init_kind"])
+        g.sweep(j["n_sweeps"], j["measure_every"])
+        g.read_series()
+        g.get_spins()
+        g.close()
+        att += WL.sites(j) * j["n_sweeps"]
+    plain = att / (time.perf_counter() - t0) / 1e9
+    return {"workload": f"first {n_jobs} jobs of the stream submitted at once; plain: first {n_plain} one at a time "
+                        "(create, initial state, sweeps, records and spins back)",
+            "served": served, "plain": plain, "ratio": served / plain, "unit": UNIT}
+
+
+def film_8_run(ig, WL):
+    """The 8^3 film over its whole run: 10^4 sweeps, a record after each."""
+    job = WL.film_8()
+    g = ig.Film(job["Lx"], job["Ly"], job["Lz"], job["J"], job["H1"], job["T"], job["seed"])
+    g.init(job["init_kind"])
+    g.synchronize()
+    t0 = time.perf_counter()
+    g.sweep(job["n_sweeps"], job["measure_every"])
+    recs = g.read_series()
+    dt = time.perf_counter() - t0
+    g.close()
+    return {"workload": "8x8x8 film, 10^4 sweeps, a record every sweep", "records": int(recs.shape[0]),
+            "attempts_per_ns": WL.sites(job) * job["n_sweeps"] / dt / 1e9, "wall_s": dt}
+
+
+def t_scan_slice(ig, WL, sweeps=4):
+    """The 40-film temperature scan (40 x 120x240x1600), a few sweeps with a
+    record after every sweep."""
+    jobs = WL.t_scan_40(n_sweeps=sweeps)
+    b = ig.Batch(jobs)
+    b.sweep(1)
+    b.synchronize()
+    t0 = time.perf_counter()
+    b.sweep(sweeps)
+    b.synchronize()
+    dt = time.perf_counter() - t0
+    b.close()
+    return {"workload": f"40 films 120x240x1600 (T = 1.5..4.4), {sweeps} sweeps with a record every sweep",
+            "attempts_per_ns": sum(WL.sites(j) for j in jobs) * sweeps / dt / 1e9, "wall_s": dt}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,7 +416,10 @@ def main():
                "note": "initial int8 lattice uploaded once from pinned memory (bytes spread over the steps); "
                        "one record read back per step"}
         for name, fn in (("batched", lambda: batched_vs_plain(ig, WL, torch)),
-                         ("serving", lambda: serving(ig, WL, n_jobs=args.serve_jobs))):
+                         ("serving", lambda: serving(ig, WL, n_jobs=args.serve_jobs)),
+                         ("serving_capacity", lambda: serving_capacity(ig, WL)),
+                         ("film_8", lambda: film_8_run(ig, WL)),
+                         ("t_scan", lambda: t_scan_slice(ig, WL))):
             try:
                 extras[name] = fn()
             except Exception as exc:  # report, never hide the main line
