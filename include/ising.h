@@ -236,11 +236,24 @@ int ising_gauss_legendre(int n, double a, double b, double *x, double *w);
 int ising_series_mean(const int64_t *records, size_t n, size_t stride, size_t col, size_t first,
                       double *mean);
 
-/* Eq. 9 as read for the literal Hamiltonian (Hn = -H1 in Eq. 1):
- * delta_f1(H1) = -integral_0^{H1} (m_1 - m_n) dH1' from n Gauss-Legendre
- * nodes on [0, H1]; m1[i], mn[i] are the per-site surface magnetisations at
- * node i.  host. */
+/* The film's own integral over its surface field: with Hn = -H1 written
+ * into Eq. 1, dF/dH1 = -(M1 - Mn), so F(H1) - F(0) = -integral_0^{H1}
+ * (m_1 - m_n) dH1' per wall site, from n Gauss-Legendre nodes on [0, H1];
+ * m1[i], mn[i] are the per-site layer magnetisations of layers 1 and Lx at
+ * node i.  In a uniform (+) film (periodic y) this is the wall term
+ * gamma+(|H1|) + gamma+(-|H1|) - 2 gamma+(0) of Eq. 21 (Eq. 7 for each
+ * wall); in a film with an interface, summed over the wall sites
+ * (M1, Mn totals), it is the F_int(H1) - F_int(0) of Eq. 21.  The Young
+ * difference of Eq. 9 is ising_ti_young_difference.  host. */
 int ising_ti_surface_field(int n, double H1, const double *m1, const double *mn, double *delta_f1);
+
+/* Eq. 9: delta_f1(H1) = -integral_0^{H1} (m_1 + m_n) dH1' from n
+ * Gauss-Legendre nodes on [0, H1], m1[i], mn[i] as above, measured in a
+ * uniform film with periodic y.  By Eqs. 4 and 7 this is
+ * f1(+)(H1) - f1(-)(H1), the difference of the two phases' surface free
+ * energies at the wall with field H1 that enters Eqs. 8 and 16 (at T = 0 it
+ * is -2 H1).  host. */
+int ising_ti_young_difference(int n, double H1, const double *m1, const double *mn, double *delta_f1);
 
 /* Eq. 19: beta F(beta_b) - beta F(beta_a) = integral U dbeta by the
  * trapezoid rule over n points (beta[i], U[i]), beta ascending or
@@ -250,6 +263,91 @@ int ising_ti_beta_trapezoid(int n, const double *beta, const double *U, double *
 /* Eq. 19 written over T: integral U dbeta = -integral U / T^2 dT, trapezoid
  * in T over n points (T[i], U[i]).  host. */
 int ising_ti_temperature_trapezoid(int n, const double *T, const double *U, double *out);
+
+/* ----------------------------------------------- interfacial analysis
+ * Host FP64 post-processing of Secs. II B - IV.  Every pointer is host
+ * memory owned by the caller; nothing is kept.  Status ISING_EINVAL for
+ * null pointers, sizes below the stated minimum or fits whose abscissae are
+ * all equal. */
+
+/* Eq. 17: mbar[kx-1] = per-site magnetisation of layer kx averaged over
+ * records first..n-1 of a (5 + Lx)-int64 record series (as ising_read_series
+ * writes it): exact integer sum of the m(kx) column, then one division by
+ * (n - first) Ly Lz. */
+int ising_layer_profile(const int64_t *records, size_t n, int Lx, int Ly, int Lz, size_t first, double *mbar);
+
+/* Eq. 12: m_minus[kx-1] = -m_plus[Lx-kx], the (-) profile from the (+) one.
+ * The arrays must not be the same. */
+int ising_mirror_profile(int Lx, const double *m_plus, double *m_minus);
+
+/* Eq. 18 with y+ + y- = Ly: y_plus[kx-1] = Ly (mbar - m-) / (m+ - m-) per
+ * layer (Lx values; m+ = m- in a layer is EINVAL).  A straight-line fit of
+ * y_plus over layers k_lo..k_hi (1 <= k_lo < k_hi <= Lx) gives the dividing
+ * plane; theta = atan(1 / |slope|), the acute angle between the plane and
+ * the walls, in (0, pi/2] (pi/2 for a plane perpendicular to the walls). */
+int ising_contact_angle(int Lx, int Ly, const double *mbar, const double *m_plus, const double *m_minus, int k_lo,
+                        int k_hi, double *y_plus, double *theta);
+
+/* Eq. 8: theta = acos(|delta_f1| / gamma_pi2), the acute Young angle.
+ * gamma_pi2 > 0; |delta_f1| > gamma_pi2 (a wet wall) is EINVAL. */
+int ising_young_angle(double delta_f1, double gamma_pi2, double *theta);
+
+/* Eq. 16 integrated from gamma(theta[0]) = gamma0 over n points: with
+ * g = gamma / sin(theta), dg/dtheta = -delta_f1 / sin^2(theta), trapezoid
+ * rule between consecutive points; gamma[i] = g_i sin(theta[i]).  theta in
+ * (0, pi), in the order the points were measured (normally from pi/2 at
+ * H1 = 0 downwards); delta_f1 in the sign of Eq. 16, where an isotropic
+ * tension gives cos(theta) = delta_f1 / gamma (so |delta_f1| of Eq. 9 for
+ * the acute angle). */
+int ising_gamma_of_theta(int n, const double *theta, const double *delta_f1, double gamma0, double *gamma);
+
+/* Eq. 19 along a path beta[0], beta[1], ... (beta > 0): beta_i F_i =
+ * beta_0 F0 + integral_{beta_0}^{beta_i} U dbeta by the trapezoid rule,
+ * F[0] = F0.  With U = U_APBC - U_PBC and beta_0 = 0.2 < beta_c, F0 = 0
+ * gives the Delta F of Eq. 20; a low-temperature start uses F0 = U0 (the
+ * ground-state energy). */
+int ising_ti_free_energy_beta(int n, const double *beta, const double *U, double F0, double *F);
+
+/* Eq. 20: least-squares line dF / (Lz Lx) = gamma_pi2 + (2 / Lx) tau0 over
+ * n >= 2 films of sizes (Lx[i], Lz[i]). */
+int ising_fit_gamma_tau(int n, const double *Lx, const double *Lz, const double *dF, double *gamma_pi2, double *tau0);
+
+/* Eq. 21 solved for its line term: R = 2 Lz [tau(H1, theta) - tau(0, pi/2)]
+ *   = dF_film - Lx Lz [gamma_theta / sin(theta) - gamma_pi2]
+ *     - Lz Ly s_wall - Lz Lx delta_f1 / tan(theta),
+ * dF_film = F_int(H1) - F_int(0) of the film with the interface (Eq. 22's
+ * integral over H1), s_wall the per-site wall term of a uniform film
+ * (ising_ti_surface_field), delta_f1 the Young difference (Eq. 9). */
+int ising_line_tension_residual(double dF_film, double Lx, double Ly, double Lz, double theta, double gamma_theta,
+                                double gamma_pi2, double s_wall, double delta_f1, double *R);
+
+/* Sec. II C's size scan: films with Lx Lz and Ly Lz held fixed differ only
+ * by 2 Lz dtau; least-squares line R = intercept + 2 dtau Lz over n >= 2
+ * films. */
+int ising_line_tension_lz_scan(int n, const double *Lz, const double *R, double *dtau, double *intercept);
+
+/* Eqs. 23-24: c from the least-squares fit gamma / gamma_pi2 - 1 =
+ * c (pi/2 - theta)^2 through the origin, kappa = gamma_pi2 (1 + 2c). */
+int ising_stiffness(int n, const double *theta, const double *gamma, double gamma_pi2, double *c, double *kappa);
+
+/* Eq. 25: C from the fit 1 - 2 kappa / (pi T) = C ((T - T_R) / T_c)^(1/2)
+ * through the origin; every T[i] > T_R. */
+int ising_roughening_kappa_fit(int n, const double *T, const double *kappa, double T_R, double T_c, double *C);
+
+/* Eq. 26 below roughening: least-squares line gamma = gamma_flat +
+ * f_s |pi/2 - theta| over n >= 2 angles near pi/2. */
+int ising_step_free_energy(int n, const double *theta, const double *gamma, double *f_s, double *gamma_flat);
+
+/* Eq. 27 with f_s proportional to 1 / xi_R: least-squares line
+ * ln f_s = log_amp - A (1 - T / T_R)^(-1/2) over n >= 2 points, T < T_R,
+ * f_s > 0. */
+int ising_roughening_fs_fit(int n, const double *T, const double *f_s, double T_R, double *A, double *log_amp);
+
+/* Eqs. 28-32, the single-step model: phi = <pi/2 - theta> =
+ * (W+1 - W-1) / (Lx Z) with W0 = 1, W+-1 = Lx exp(-f_s Lz / T)
+ * exp(+-2 H1 Lz / T), evaluated relative to the largest weight (no
+ * overflow); h1_star = f_s / 2 - T ln(Lx) / (2 Lz).  T, Lx, Lz > 0. */
+int ising_step_model(double H1, double f_s, double T, double Lx, double Lz, double *phi, double *h1_star);
 
 /* ------------------------------------- measurement without allocation */
 

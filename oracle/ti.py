@@ -1,10 +1,10 @@
 """Thermodynamic-integration arithmetic of the paper -- TEST INFRASTRUCTURE ONLY.
 
 Plain numpy restatement, independent of the product's C implementation:
-  Eq. 9  (Sec. II A): delta_f1 = -integral_0^{H1} [m_1 + m_n] dH1'.  With
-         Hn = -H1 written literally into Eq. 1, dF/dH1 = -<M1> + <Mn>, so the
-         integrand in terms of the measured layer sums is m_1 - m_n (m_n taken
-         with the sign of its own field Hn = -H1 gives the paper's m_1 + m_n).
+  The film's own integral over H1: with Hn = -H1 written into Eq. 1,
+         dF/dH1 = -<M1> + <Mn>, so F(H1) - F(0) = -integral_0^{H1}
+         (m_1 - m_n) dH1'.  In a uniform film this is the wall term of Eq. 21;
+         the Young difference of Eq. 9 (m_1 + m_n) is in oracle/analysis.py.
   Eq. 19 (Sec. II C): beta F(beta) - beta0 F(beta0) = integral U dbeta, by the
          trapezoid rule in beta, or over T as -integral U / T^2 dT.
 Gauss-Legendre nodes come from numpy's library routine.
@@ -27,7 +27,7 @@ def series_mean(records, col, first=0):
 
 
 def surface_field_ti(H1, m1, mn):
-    """Eq. 9 over Gauss-Legendre nodes on [0, H1] (m1, mn per site at each node)."""
+    """-integral_0^{H1} (m1 - mn) over Gauss-Legendre nodes on [0, H1]."""
     x, w = gauss_legendre(len(m1), 0.0, H1)
     return -float(np.sum(w * (np.asarray(m1, dtype=np.float64) - np.asarray(mn, dtype=np.float64))))
 

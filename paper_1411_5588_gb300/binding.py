@@ -93,6 +93,21 @@ _SIGS = {
     "ising_ti_surface_field": [_c.c_int, _c.c_double, P, P, DP],
     "ising_ti_beta_trapezoid": [_c.c_int, P, P, DP],
     "ising_ti_temperature_trapezoid": [_c.c_int, P, P, DP],
+    "ising_ti_young_difference": [_c.c_int, _c.c_double, P, P, DP],
+    "ising_layer_profile": [P, _c.c_size_t, _c.c_int, _c.c_int, _c.c_int, _c.c_size_t, P],
+    "ising_mirror_profile": [_c.c_int, P, P],
+    "ising_contact_angle": [_c.c_int, _c.c_int, P, P, P, _c.c_int, _c.c_int, P, DP],
+    "ising_young_angle": [_c.c_double, _c.c_double, DP],
+    "ising_gamma_of_theta": [_c.c_int, P, P, _c.c_double, P],
+    "ising_ti_free_energy_beta": [_c.c_int, P, P, _c.c_double, P],
+    "ising_fit_gamma_tau": [_c.c_int, P, P, P, DP, DP],
+    "ising_line_tension_residual": [_c.c_double] * 9 + [DP],
+    "ising_line_tension_lz_scan": [_c.c_int, P, P, DP, DP],
+    "ising_stiffness": [_c.c_int, P, P, _c.c_double, DP, DP],
+    "ising_roughening_kappa_fit": [_c.c_int, P, P, _c.c_double, _c.c_double, DP],
+    "ising_step_free_energy": [_c.c_int, P, P, DP, DP],
+    "ising_roughening_fs_fit": [_c.c_int, P, P, _c.c_double, DP, DP],
+    "ising_step_model": [_c.c_double] * 5 + [DP, DP],
     "ising_measure_packed_noalloc": [P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64, P, P],
     "ising_strerror": [_c.c_int],
     "ising_last_error": [],

@@ -161,7 +161,7 @@ def test_mixed_batch_matches_films_run_alone():
 
 
 def test_thermodynamic_integration_from_gpu_records_matches_oracle():
-    """Eq. 9 over 8 Gauss-Legendre nodes in H1: the FP64 result from the GPU's
+    """The film's own integral over H1 (8 Gauss-Legendre nodes): the FP64 result from the GPU's
     records through the library equals the oracle-fed numpy result to 1e-12."""
     from oracle import ti as OT
     H1max, n = 0.6, 8
