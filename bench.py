@@ -316,6 +316,62 @@ def t_scan_slice(ig, WL, sweeps=4):
             "attempts_per_ns": sum(WL.sites(j) for j in jobs) * sweeps / dt / 1e9, "wall_s": dt}
 
 
+def procedures(ig, WL):
+    """The paper's procedures at their default sizes, each film set in one
+    batch. It runs the beta integration for gamma(pi/2) and tau(0, pi/2), then
+    the contact angle, Young difference and gamma(theta) scan, then stiffness
+    and step free energy, then the line tension over a constant-area set.
+    Sweeps are timed on the device side (synchronised wall clock) and the
+    host reductions separately."""
+    import numpy as np
+
+    from paper_1411_5588_gb300 import workflows as PW
+
+    def timed_run(wl):
+        b = ig.Batch(wl["jobs"])
+        b.synchronize()
+        t0 = time.perf_counter()
+        b.sweep(wl["n_sweeps"], True)
+        b.synchronize()
+        dt = time.perf_counter() - t0
+        recs = [b.read_series(i) for i in range(len(wl["jobs"]))]
+        b.close()
+        att = sum(WL.sites(j) for j in wl["jobs"]) * wl["n_sweeps"]
+        return recs, {"films": len(wl["jobs"]), "attempts": att, "sweep_s": dt, "attempts_per_ns": att / dt / 1e9}
+
+    out = {}
+    it = WL.interface_tension_set()
+    recs, out["interface_tension_run"] = timed_run(it)
+    t0 = time.perf_counter()
+    r_it = PW.interface_tension(it, recs)
+    out["interface_tension"] = {"sizes": it["sizes"], "Ly": it["Ly"], "T": it["T"], "n_beta": len(it["betas"]),
+                                "dF": r_it["dF"].tolist(), "gamma_pi2": r_it["gamma_pi2"], "tau0": r_it["tau0"],
+                                "host_s": time.perf_counter() - t0}
+    ca = WL.contact_angle_set()
+    recs, out["contact_angle_run"] = timed_run(ca)
+    t0 = time.perf_counter()
+    r_ca = PW.contact_angle(ca, recs, r_it["gamma_pi2"])
+    r_st = PW.stiffness_and_steps(r_ca["theta"], r_ca["gamma"], r_it["gamma_pi2"], ca["T"], ca["Lx"], ca["Lz"],
+                                  ca["H1s"])
+    out["contact_angle"] = {"film": [ca["Lx"], ca["Ly"], ca["Lz"]], "T": ca["T"], "H1": list(ca["H1s"]),
+                            "theta_deg": np.degrees(r_ca["theta"]).tolist(),
+                            "theta_young_deg": np.degrees(r_ca["theta_young"]).tolist(),
+                            "delta_f1": r_ca["delta_f1"].tolist(), "gamma": r_ca["gamma"].tolist(),
+                            "stiffness_c": r_st["c"], "kappa": r_st["kappa"], "f_s": r_st["f_s"],
+                            "host_s": time.perf_counter() - t0}
+    lt = WL.line_tension_set()
+    j = list(ca["H1s"]).index(lt["H1"])
+    recs, out["line_tension_run"] = timed_run(lt)
+    t0 = time.perf_counter()
+    r_lt = PW.line_tension(lt, recs, r_ca["theta"][j], r_ca["gamma"][j], r_it["gamma_pi2"])
+    out["line_tension"] = {"sizes": [list(v) for v in lt["sizes"]], "H1": lt["H1"], "R": r_lt["R"].tolist(),
+                           "dtau": r_lt["dtau"], "intercept": r_lt["intercept"], "host_s": time.perf_counter() - t0}
+    runs = [out[k] for k in ("interface_tension_run", "contact_angle_run", "line_tension_run")]
+    out["attempts_per_ns"] = sum(r["attempts"] for r in runs) / sum(r["sweep_s"] for r in runs) / 1e9
+    out["unit"] = UNIT
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,7 +475,8 @@ def main():
                          ("serving", lambda: serving(ig, WL, n_jobs=args.serve_jobs)),
                          ("serving_capacity", lambda: serving_capacity(ig, WL)),
                          ("film_8", lambda: film_8_run(ig, WL)),
-                         ("t_scan", lambda: t_scan_slice(ig, WL))):
+                         ("t_scan", lambda: t_scan_slice(ig, WL)),
+                         ("procedures", lambda: procedures(ig, WL))):
             try:
                 extras[name] = fn()
             except Exception as exc:  # report, never hide the main line

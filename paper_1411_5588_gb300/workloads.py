@@ -17,12 +17,25 @@ Both the CUDA path and the CPU oracle are driven from these lists.
               in [500, 5000], seed 3
   t_scan_40   40 films 120 x 240 x 1600 at T = 1.5 .. 4.4 (step 0.0744),
               H1 = 0.55, slab start (seed 5), records every sweep
+
+The three film sets of the paper's procedures (Secs. II B, II C, III, IV);
+``roles`` tags each film with what it measures:
+  contact_angle_set     per H1: the film with the Eq. 11 boundary from a
+                        slab start ("interface"), a periodic-y film from all
+                        up ("plus", the (+) plateaus), and periodic-y films at
+                        n_gl Gauss-Legendre nodes of [0, H1] ("node")
+  interface_tension_set per size Lx = Lz and per beta on a grid from 0.2:
+                        antiperiodic ("apbc") and periodic ("pbc") y, H1 = 0
+  line_tension_set      per size of a constant-area set (Lx Lz and Ly Lz
+                        fixed): films with the Eq. 11 boundary ("interface")
+                        and periodic-y films ("plus") at the nodes of [0, H1]
 """
 from __future__ import annotations
 
 import numpy as np
 
-Y_GAPBC, INIT_RANDOM, INIT_SLAB_Y = 0, 0, 1
+Y_GAPBC, Y_PBC, Y_APBC = 0, 1, 2
+INIT_RANDOM, INIT_SLAB_Y, INIT_ALL_UP = 0, 1, 2
 
 
 def film_8():
@@ -82,3 +95,55 @@ def t_scan_40(n_sweeps=10000):
 
 def sites(job):
     return int(job["Lx"]) * int(job["Ly"]) * int(job["Lz"])
+
+
+def _nodes(n, a, b):
+    t, _ = np.polynomial.legendre.leggauss(int(n))
+    return 0.5 * (b - a) * (t + 1.0) + a
+
+
+def _film(Lx, Ly, Lz, T, H1, seed, replica, y_mode, init_kind, n_sweeps):
+    return dict(Lx=int(Lx), Ly=int(Ly), Lz=int(Lz), J=1.0, H1=float(H1), T=float(T), seed=int(seed),
+                replica=int(replica), y_mode=y_mode, init_kind=init_kind, flip_p=0.0, measure_every=1,
+                n_sweeps=int(n_sweeps))
+
+
+def contact_angle_set(Lx=32, Ly=96, Lz=64, T=3.0, H1s=(0.15, 0.3, 0.45, 0.55), n_gl=8, n_sweeps=2000,
+                      first=500, seed=7):
+    jobs, roles = [], []
+    for j, h in enumerate(H1s):
+        jobs.append(_film(Lx, Ly, Lz, T, h, seed, len(jobs), Y_GAPBC, INIT_SLAB_Y, n_sweeps))
+        roles.append(("interface", j))
+        jobs.append(_film(Lx, Ly, Lz, T, h, seed, len(jobs), Y_PBC, INIT_ALL_UP, n_sweeps))
+        roles.append(("plus", j))
+        for i, x in enumerate(_nodes(n_gl, 0.0, h)):
+            jobs.append(_film(Lx, Ly, Lz, T, x, seed, len(jobs), Y_PBC, INIT_ALL_UP, n_sweeps))
+            roles.append(("node", j, i))
+    return dict(kind="contact_angle", Lx=Lx, Ly=Ly, Lz=Lz, T=T, H1s=tuple(float(h) for h in H1s), n_gl=n_gl,
+                n_sweeps=n_sweeps, first=first, jobs=jobs, roles=roles)
+
+
+def interface_tension_set(sizes=(20, 30, 40), Ly=60, T=3.0, beta0=0.2, n_beta=24, n_sweeps=2000, first=500,
+                          seed=8):
+    betas = np.linspace(beta0, 1.0 / T, n_beta)
+    jobs, roles = [], []
+    for s, L in enumerate(sizes):
+        for k, b in enumerate(betas):
+            for name, mode in (("apbc", Y_APBC), ("pbc", Y_PBC)):
+                jobs.append(_film(L, Ly, L, 1.0 / b, 0.0, seed, len(jobs), mode, INIT_ALL_UP, n_sweeps))
+                roles.append((name, s, k))
+    return dict(kind="interface_tension", sizes=tuple(sizes), Ly=Ly, T=T, betas=betas, n_sweeps=n_sweeps,
+                first=first, jobs=jobs, roles=roles)
+
+
+def line_tension_set(sizes=((32, 128, 16), (16, 64, 32), (8, 32, 64)), T=3.0, H1=0.45, n_gl=8, n_sweeps=2000,
+                     first=500, seed=9):
+    jobs, roles = [], []
+    for s, (Lx, Ly, Lz) in enumerate(sizes):
+        for i, x in enumerate(_nodes(n_gl, 0.0, H1)):
+            jobs.append(_film(Lx, Ly, Lz, T, x, seed, len(jobs), Y_GAPBC, INIT_SLAB_Y, n_sweeps))
+            roles.append(("interface", s, i))
+            jobs.append(_film(Lx, Ly, Lz, T, x, seed, len(jobs), Y_PBC, INIT_ALL_UP, n_sweeps))
+            roles.append(("plus", s, i))
+    return dict(kind="line_tension", sizes=tuple(tuple(v) for v in sizes), T=T, H1=float(H1), n_gl=n_gl,
+                n_sweeps=n_sweeps, first=first, jobs=jobs, roles=roles)
