@@ -68,6 +68,7 @@ enum {
 enum { ISING_Y_GAPBC = 0, ISING_Y_PBC = 1, ISING_Y_APBC = 2 };
 enum { ISING_X_FREE = 0, ISING_X_PBC = 1 };
 enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
+enum { ISING_PATH_AUTO = 0, ISING_PATH_GRID = 1, ISING_PATH_RESIDENT = 2 };
 
 typedef struct ising ising;
 
@@ -119,6 +120,14 @@ int ising_set_packed_device(ising *h, const uint32_t *src);
  * chain bit-exactly; it must stay below 0xFFFFFFFF. */
 int ising_get_sweep(const ising *h, uint64_t *sweep);
 int ising_set_sweep(ising *h, uint64_t sweep);
+
+/* Which kernels run ising_sweep (the chain and its records are identical
+ * either way).  GRID: two grid-wide launches per sweep (plus the record
+ * kernels), for any size.  RESIDENT: the whole call in one launch of one
+ * block that keeps the packed film in shared memory, for small films (at
+ * most 65536 spins whose planes fit in 48 KiB); EINVAL for a larger film.
+ * AUTO (the default): RESIDENT up to 32768 spins, else GRID. */
+int ising_set_path(ising *h, int path);
 
 /* Enqueue n_sweeps sweeps on the handle's stream (asynchronous).  After every
  * sweep whose count of completed sweeps is a multiple of measure_every (> 0)

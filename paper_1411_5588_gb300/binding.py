@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = range(7)
 Y_GAPBC, Y_PBC, Y_APBC = 0, 1, 2
 X_FREE, X_PBC = 0, 1
 INIT_RANDOM, INIT_SLAB_Y, INIT_ALL_UP = 0, 1, 2
+PATH_AUTO, PATH_GRID, PATH_RESIDENT = 0, 1, 2
 
 _c = ctypes
 P = _c.c_void_p
@@ -56,6 +57,7 @@ _SIGS = {
     "ising_create": [_c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double, _c.c_uint64,
                      _c.POINTER(P)],
     "ising_set_options": [P, _c.c_int, _c.c_int, _c.c_double, _c.c_uint32],
+    "ising_set_path": [P, _c.c_int],
     "ising_set_params": [P, _c.c_double, _c.c_double, _c.c_double],
     "ising_set_stream": [P, P],
     "ising_init": [P, _c.c_int, _c.c_double],
@@ -162,7 +164,7 @@ class Film:
     """One film (``ising_create`` ... ``ising_destroy``)."""
 
     def __init__(self, Lx, Ly, Lz, J=1.0, H1=0.0, T=3.0, seed=1, *, y_mode=Y_GAPBC, x_mode=X_FREE, H=0.0,
-                 replica=0, stream=None):
+                 replica=0, stream=None, path=PATH_AUTO):
         self.Lx, self.Ly, self.Lz = int(Lx), int(Ly), int(Lz)
         self.J, self.H1, self.T, self.H = float(J), float(H1), float(T), float(H)
         h = P()
@@ -172,6 +174,11 @@ class Film:
         check(lib().ising_set_options(h, int(y_mode), int(x_mode), self.H, int(replica)), "ising_set_options")
         if stream is not None:
             check(lib().ising_set_stream(h, _torch_stream(stream)), "ising_set_stream")
+        if path != PATH_AUTO:
+            self.set_path(path)
+
+    def set_path(self, path):
+        check(lib().ising_set_path(self._h, int(path)), "ising_set_path")
 
     def close(self):
         if getattr(self, "_h", None):

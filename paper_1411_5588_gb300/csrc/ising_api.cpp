@@ -248,6 +248,7 @@ struct ising {
   int64_t* d_direct = nullptr;
   int8_t* d_stage = nullptr;
   bool dirty = true;
+  int path = ISING_PATH_AUTO;
   FilmDesc& d() { return fs.h[0]; }
 };
 
@@ -476,6 +477,17 @@ int ising_set_sweep(ising* h, uint64_t sweep) {
   return sync_desc(h);
 }
 
+int ising_set_path(ising* h, int path) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  if (path != ISING_PATH_AUTO && path != ISING_PATH_GRID && path != ISING_PATH_RESIDENT)
+    return fail(ISING_EINVAL, "unknown path %d", path);
+  if (path == ISING_PATH_RESIDENT && !resident_smem_bytes(h->d()))
+    return fail(ISING_EINVAL, "film too large for the resident path");
+  h->path = path;
+  return ISING_OK;
+}
+
 int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
   clear_error();
   if (!h) return fail(ISING_EINVAL, "NULL handle");
@@ -492,6 +504,18 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
   if (rc) return rc;
   rc = sync_desc(h);
   if (rc) return rc;
+  const bool auto_ok = (uint64_t)d.Lx * d.Ly * d.Lz <= kResidentAutoSites;
+  const uint32_t smem = (h->path == ISING_PATH_RESIDENT || (h->path == ISING_PATH_AUTO && auto_ok))
+                            ? resident_smem_bytes(d) : 0u;
+  if (smem) {
+    // small film: every sweep of the call in one launch, planes in shared memory
+    ISG_CK(launch_resident(h->fs.L.films, 1, smem, resident_threads(d), d.has_never != 0, h->fs.pool, h->fs.rec,
+                           (uint32_t)n, h->fs.stream));
+    d.sweep = (uint32_t)(s0 + n);
+    d.rec_next += (uint32_t)nrec;
+    h->rec_written += nrec;
+    return ISING_OK;
+  }
   // single film: the descriptor travels as a kernel parameter
   for (uint64_t k = 0; k < n; k++) {
     const uint32_t t = (uint32_t)(s0 + k);

@@ -330,6 +330,47 @@ __device__ __forceinline__ int bonds(uint32_t a, uint32_t b, uint32_t valid, int
   return nv - 2 * __popc((a ^ b) & valid);
 }
 
+// Record contributions of word w of row (kxm1, kym1) (0-based) of the planes
+// A (z0 even) and B (z0 odd) with row stride Wp: the magnetisation of its
+// sites and their +x, +y (Eq. 11 wrap: partner row, sign -1 unless PBC) and
+// +z bonds.
+__device__ __forceinline__ void measure_word(const uint32_t* A, const uint32_t* B, uint32_t Wp, uint32_t Lx,
+                                             uint32_t Ly, uint32_t W, uint32_t n, uint32_t last_mask, uint32_t x_pbc,
+                                             uint32_t y_mode, uint32_t kxm1, uint32_t kym1, uint32_t w, int& m,
+                                             int& bb) {
+  const uint32_t row = kxm1 * Ly + kym1;
+  const size_t base = (size_t)row * Wp + w;
+  const bool last = (w + 1 == W);
+  const uint32_t valid = last ? last_mask : 0xFFFFFFFFu;
+  const int nv = __popc(valid);
+  const uint32_t a = A[base], b = B[base];
+  m = 2 * (__popc(a & valid) + __popc(b & valid)) - 2 * nv;
+  bb = 0;
+  // +x bond
+  if (kxm1 + 1 < Lx) {
+    const size_t nb = base + (size_t)Ly * Wp;
+    bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
+  } else if (x_pbc) {
+    const size_t nb = base - (size_t)(Lx - 1) * Ly * Wp;
+    bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
+  }
+  // +y bond
+  if (kym1 + 1 < Ly) {
+    bb += bonds(a, A[base + Wp], valid, nv) + bonds(b, B[base + Wp], valid, nv);
+  } else {
+    const uint32_t gkx = (y_mode == kYGapbc) ? (Lx - 1 - kxm1) : kxm1;
+    const size_t g = ((size_t)gkx * Ly) * Wp + w;
+    const int y = bonds(a, A[g], valid, nv) + bonds(b, B[g], valid, nv);
+    bb += (y_mode != kYPbc) ? -y : y;
+  }
+  // +z bonds: (2j, 2j+1) inside the word pair, (2j+1, 2j+2) through a shift
+  bb += bonds(a, b, valid, nv);
+  const size_t rbase = (size_t)row * Wp;
+  uint32_t an = shift_next(a, last ? A[rbase] : A[base + 1]);
+  if (last && last_mask != 0xFFFFFFFFu) an |= (A[rbase] & 1u) << bitpos((n - 1) & 31u);
+  bb += bonds(b, an, valid, nv);
+}
+
 __device__ __forceinline__ bool measured_now(const FilmDesc& F, uint32_t done, int force) {
   if (force) return true;
   if (F.measure_every == 0 || done == 0 || F.sweep_end - F.sweep < done) return false;
@@ -353,41 +394,11 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
     const uint32_t Wp = F.Wp;
     const uint32_t* A = pool + F.spin_off;
     const uint32_t* B = A + (size_t)Lx * Ly * Wp;
-    const bool neg = F.y_mode != kYPbc;
-    const uint32_t gkx = (F.y_mode == kYGapbc) ? (Lx - 1 - kxm1) : kxm1;
     int64_t msum = 0, bsum = 0;
     for (uint32_t it = chunk * blockDim.x + threadIdx.x; it < Ly * W; it += bpl * blockDim.x) {
       const uint32_t kym1 = it / W, w = it % W;
-      const uint32_t row = kxm1 * Ly + kym1;
-      const size_t base = (size_t)row * Wp + w;
-      const bool last = (w + 1 == W);
-      const uint32_t valid = last ? F.last_mask : 0xFFFFFFFFu;
-      const int nv = __popc(valid);
-      const uint32_t a = A[base], b = B[base];
-      int m = 2 * (__popc(a & valid) + __popc(b & valid)) - 2 * nv;
-      int bb = 0;
-      // +x bond
-      if (kxm1 + 1 < Lx) {
-        const size_t nb = base + (size_t)Ly * Wp;
-        bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
-      } else if (F.x_pbc) {
-        const size_t nb = base - (size_t)(Lx - 1) * Ly * Wp;
-        bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
-      }
-      // +y bond (wrap: the Eq. 11 partner row, sign -1 unless PBC)
-      if (kym1 + 1 < Ly) {
-        bb += bonds(a, A[base + Wp], valid, nv) + bonds(b, B[base + Wp], valid, nv);
-      } else {
-        const size_t g = ((size_t)gkx * Ly) * Wp + w;
-        const int y = bonds(a, A[g], valid, nv) + bonds(b, B[g], valid, nv);
-        bb += neg ? -y : y;
-      }
-      // +z bonds: (2j, 2j+1) inside the word pair, (2j+1, 2j+2) through a shift
-      bb += bonds(a, b, valid, nv);
-      const size_t rbase = (size_t)row * Wp;
-      uint32_t an = shift_next(a, last ? A[rbase] : A[base + 1]);
-      if (last && F.last_mask != 0xFFFFFFFFu) an |= (A[rbase] & 1u) << bitpos((F.n - 1) & 31u);
-      bb += bonds(b, an, valid, nv);
+      int m, bb;
+      measure_word(A, B, Wp, Lx, Ly, W, F.n, F.last_mask, F.x_pbc, F.y_mode, kxm1, kym1, w, m, bb);
       msum += m;
       bsum += bb;
     }
@@ -445,6 +456,129 @@ __global__ void advance_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __
     if (!films[f].active) continue;
     const uint32_t s = films[f].sweep, e = films[f].sweep_end;
     films[f].sweep = (e - s < n_sweeps) ? e : s + n_sweeps;
+  }
+}
+
+// ------------------------------------------------------------ resident path
+
+// All sweeps of a run for one small film per block.  The planes are copied
+// into shared memory once (row stride W), each half-sweep is the same block
+// body as the grid kernels followed by a block barrier (the next colour reads
+// what this one wrote), the records of the run go straight into the film's
+// ring, and the planes, sweep and rec_next are written back at the end.
+template <bool FAST>
+__global__ void __launch_bounds__(kResidentThreads, 1)
+resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64_t* __restrict__ records,
+                uint32_t n_sweeps) {
+  extern __shared__ __align__(16) uint32_t s_planes[];
+  constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
+  __shared__ __align__(16) FilmDesc s_d;
+  __shared__ __align__(16) uint32_t s_thr[64];
+  __shared__ __align__(16) uint32_t s_alw[64];
+  __shared__ int64_t s_red[kResidentThreads / 32];
+  FilmDesc* Fg = films + blockIdx.x;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Fg);
+    uint4* dst = reinterpret_cast<uint4*>(&s_d);
+    for (uint32_t i = threadIdx.x; i < kDescWords / 4; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
+    const bool a = (s_d.always[i >> 4] >> (i & 15)) & 1u;
+    s_thr[i] = FAST ? (a ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
+    s_alw[i] = a ? 0xFFFFFFFFu : 0u;
+  }
+  if (!s_d.active) return;  // the same for the whole block
+  const uint32_t Lx = s_d.Lx, Ly = s_d.Ly, W = s_d.W, Wp = s_d.Wp;
+  const uint32_t words = Lx * Ly * W;  // one plane in shared memory
+  int* s_m = reinterpret_cast<int*>(s_planes + 2 * words);
+  uint32_t* g0 = pool + s_d.spin_off;
+  uint32_t* g1 = g0 + (size_t)Lx * Ly * Wp;
+  for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
+    const uint32_t X = i >= words ? 1u : 0u;
+    const uint32_t rw = i - X * words, r = rw / W, w = rw - r * W;
+    s_planes[i] = (X ? g1 : g0)[(size_t)r * Wp + w];
+  }
+  __syncthreads();
+  FilmCtx c;
+  c.Lx = Lx; c.Ly = Ly; c.n = s_d.n; c.W = W; c.Wp = W;
+  c.y_mode = s_d.y_mode; c.x_pbc = s_d.x_pbc; c.rk0 = s_d.rk0; c.rk1 = s_d.rk1;
+  c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
+  c.plane0 = s_planes;
+  c.plane1 = s_planes + words;
+  const uint32_t items = s_d.upd_items;
+  const uint32_t m_every = s_d.measure_every;
+  uint32_t rec_next = s_d.rec_next;
+  uint32_t done = 0;
+  for (uint32_t k = 0; k < n_sweeps; k++) {
+    const uint32_t t = s_d.sweep + k;
+    if (t >= s_d.sweep_end) break;
+    c.sweep = t;
+    for (uint32_t colour = 0; colour < 2; colour++) {
+      c.colour = colour;
+      for (uint32_t item = threadIdx.x; item < items; item += blockDim.x) {
+        uint32_t kx, ky, w;
+        item_word(c, item, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, kx, ky, w);
+        Fetched f;
+        fetch_word(c, kx, ky, w, f);
+        update_fetched<FAST>(c, f, s_thr, s_alw);
+      }
+      __syncthreads();
+    }
+    done = k + 1;
+    if (m_every == 0 || (t + 1) % m_every != 0) continue;
+    // record of sweep t + 1: layer sums in shared memory, bond sum reduced
+    for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) s_m[kx] = 0;
+    __syncthreads();
+    int64_t bsum = 0;
+    const uint32_t total = Lx * Ly * W;
+    for (uint32_t base = 0; base < total; base += blockDim.x) {
+      const uint32_t it = base + threadIdx.x;
+      const bool on = it < total;
+      int m = 0, bb = 0;
+      uint32_t kxm1 = 0xFFFFFFFFu;
+      if (on) {
+        const uint32_t row = it / W, w = it - row * W;
+        kxm1 = row / Ly;
+        measure_word(c.plane0, c.plane1, W, Lx, Ly, W, c.n, c.last_mask, c.x_pbc, c.y_mode, kxm1, row - kxm1 * Ly,
+                     w, m, bb);
+        bsum += bb;
+      }
+      // one atomic per warp when the warp's words share a layer
+      const uint32_t k0 = __shfl_sync(0xFFFFFFFFu, kxm1, 0);
+      if (__all_sync(0xFFFFFFFFu, !on || kxm1 == k0)) {
+        int v = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if ((threadIdx.x & 31u) == 0 && k0 != 0xFFFFFFFFu) atomicAdd(&s_m[k0], v);
+      } else if (on) {
+        atomicAdd(&s_m[kxm1], m);
+      }
+    }
+    const int64_t tb = block_sum(bsum, s_red);  // its barriers also complete s_m
+    const uint32_t slot = s_d.rec_cap ? rec_next % s_d.rec_cap : 0u;
+    int64_t* rec = records + s_d.rec_off + (size_t)slot * (5 + Lx);
+    for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) rec[5 + kx] = s_m[kx];
+    if (threadIdx.x == 0) {
+      int64_t M = 0;
+      for (uint32_t kx = 0; kx < Lx; kx++) M += s_m[kx];
+      rec[0] = (int64_t)t + 1;
+      rec[1] = tb;
+      rec[2] = M;
+      rec[3] = s_m[0];
+      rec[4] = s_m[Lx - 1];
+    }
+    rec_next++;
+    __syncthreads();  // s_m is read above before the next record clears it
+  }
+  for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
+    const uint32_t X = i >= words ? 1u : 0u;
+    const uint32_t rw = i - X * words, r = rw / W, w = rw - r * W;
+    (X ? g1 : g0)[(size_t)r * Wp + w] = s_planes[i];
+  }
+  if (threadIdx.x == 0) {
+    Fg->sweep = s_d.sweep + done;
+    Fg->rec_next = rec_next;
   }
 }
 
@@ -565,6 +699,28 @@ cudaError_t launch_pack(const FilmDesc& f, uint32_t* pool, const int8_t* s, cuda
 cudaError_t launch_unpack(const FilmDesc& f, const uint32_t* pool, int8_t* s, cudaStream_t st) {
   const size_t n = (size_t)f.Lx * f.Ly * f.Lz;
   unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, pool, s);
+  return cudaGetLastError();
+}
+
+uint32_t resident_smem_bytes(const FilmDesc& d) {
+  const uint64_t sites = (uint64_t)d.Lx * d.Ly * d.Lz;
+  const uint64_t bytes = 4ull * (2ull * d.Lx * d.Ly * d.W + d.Lx);
+  if (sites > kResidentMaxSites || bytes > kResidentMaxSmem) return 0;
+  return (uint32_t)bytes;
+}
+
+uint32_t resident_threads(const FilmDesc& d) {
+  const uint32_t t = ((d.upd_items + 31u) / 32u) * 32u;
+  return t < 32u ? 32u : (t > kResidentThreads ? kResidentThreads : t);
+}
+
+cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_bytes, uint32_t threads, bool exact,
+                            uint32_t* pool, int64_t* records, uint32_t n_sweeps, cudaStream_t st) {
+  if (n_films == 0 || n_sweeps == 0) return cudaSuccess;
+  if (smem_bytes > kResidentMaxSmem || threads == 0 || threads > kResidentThreads || threads % 32u)
+    return cudaErrorInvalidValue;
+  if (exact) resident_kernel<false><<<n_films, threads, smem_bytes, st>>>(films, pool, records, n_sweeps);
+  else resident_kernel<true><<<n_films, threads, smem_bytes, st>>>(films, pool, records, n_sweeps);
   return cudaGetLastError();
 }
 

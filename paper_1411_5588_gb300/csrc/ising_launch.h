@@ -20,6 +20,18 @@ constexpr int kMeasureBlock = 256;
 // Items a measurement block covers per layer before another block is added.
 constexpr uint32_t kMeasureItemsPerBlock = 4 * kMeasureBlock;
 
+// Resident path: one block per film holds the film's packed planes in shared
+// memory (row stride W) for a whole run of sweeps, records included.  Films
+// up to kResidentMaxSites spins whose planes and layer sums fit in
+// kResidentMaxSmem bytes qualify; larger ones use the per-half-sweep grid.
+// Chosen automatically up to kResidentAutoSites: beyond that one SM's issue
+// rate loses to the grid kernels (about 16 us per sweep there without
+// records, 27 us with one every sweep).
+constexpr uint32_t kResidentThreads = 512;
+constexpr uint64_t kResidentMaxSites = 1ull << 16;
+constexpr uint64_t kResidentAutoSites = 1ull << 15;
+constexpr uint32_t kResidentMaxSmem = 48u * 1024u;
+
 // Device arrays describing the films of a launch.
 struct LaunchSet {
   FilmDesc* films = nullptr;         // n_films descriptors
@@ -42,6 +54,15 @@ cudaError_t launch_init(const FilmDesc& f, uint32_t* pool, int kind, uint32_t fl
                         cudaStream_t st);
 cudaError_t launch_pack(const FilmDesc& f, uint32_t* pool, const int8_t* s, cudaStream_t st);
 cudaError_t launch_unpack(const FilmDesc& f, const uint32_t* pool, int8_t* s, cudaStream_t st);
+// Dynamic shared memory of a film on the resident path, 0 if it does not qualify.
+uint32_t resident_smem_bytes(const FilmDesc& d);
+// Threads per block for a film on the resident path (a multiple of 32).
+uint32_t resident_threads(const FilmDesc& d);
+// n_sweeps sweeps (with their records) of films[0..n_films) on the resident
+// path, one block each; every film must qualify, smem_bytes and threads cover
+// the largest.  The kernel advances each descriptor's sweep and rec_next.
+cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_bytes, uint32_t threads, bool exact,
+                            uint32_t* pool, int64_t* records, uint32_t n_sweeps, cudaStream_t st);
 int update_blocks_per_sm();
 int measure_blocks_per_sm();
 

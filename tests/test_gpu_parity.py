@@ -38,18 +38,21 @@ CASES = [
 ]
 
 
-def _pair(case, seed=7, replica=3):
+def _pair(case, seed=7, replica=3, path=ig.PATH_AUTO):
     Lx, Ly, Lz, ym, xm, H1, H, T, kind, flip = case
-    g = ig.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica)
+    g = ig.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica, path=path)
     o = O.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica)
     g.init(kind, flip)
     o.init(kind, flip)
     return g, o
 
 
+@pytest.mark.parametrize("path", [ig.PATH_GRID, ig.PATH_RESIDENT], ids=["grid", "resident"])
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-y{c[3]}x{c[4]}-T{c[7]}" for c in CASES])
-def test_sweeps_bit_exact(case):
-    g, o = _pair(case)
+def test_sweeps_bit_exact(case, path):
+    """Both single-film paths: the grid kernels (two launches per sweep) and
+    the resident kernel (the film in shared memory for the whole call)."""
+    g, o = _pair(case, path=path)
     assert np.array_equal(g.get_spins(), o.get_spins()), "initial state differs"
     done = 0
     for n, m in ((1, 1), (1, 1), (8, 2), (90, 3)):
@@ -186,3 +189,21 @@ def test_thermodynamic_integration_from_gpu_records_matches_oracle():
     c = OT.surface_field_ti(H1max, m1o, mno)
     assert abs(a - c) <= 1e-12 * abs(c)
     b.close()
+
+
+def test_resident_path_limits():
+    """AUTO picks the resident kernel only for films it can hold; forcing it
+    on a larger film is refused, and a film can switch paths mid-chain."""
+    big = ig.Film(64, 64, 32, 1.0, 0.5, 3.0, 1)  # 131072 spins
+    with pytest.raises(ig.IsingError) as e:
+        big.set_path(ig.PATH_RESIDENT)
+    assert e.value.status == ig.EINVAL
+    big.close()
+    case = (12, 10, 40, ig.Y_GAPBC, ig.X_FREE, 0.55, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01)
+    g, o = _pair(case)
+    for path, n, m in ((ig.PATH_RESIDENT, 7, 2), (ig.PATH_GRID, 5, 3), (ig.PATH_RESIDENT, 11, 1)):
+        g.set_path(path)
+        g.sweep(n, m)
+        assert np.array_equal(g.read_series(), o.sweep(n, m))
+        assert np.array_equal(g.get_spins(), o.get_spins())
+    g.close()
