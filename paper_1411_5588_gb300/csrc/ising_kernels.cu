@@ -20,6 +20,13 @@ namespace isg {
 
 namespace {
 
+// Programmatic dependent launch: every kernel of the sweep path lets the next
+// launch of its stream start early (its blocks then sit in pdl_wait) and
+// waits, before it touches any film state, for the previous grid to complete
+// and its writes to be visible.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
   return (a & b) | (c & (a ^ b));
 }
@@ -252,6 +259,8 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
   __shared__ __align__(16) FilmDesc s_d;
   __shared__ __align__(16) uint32_t s_alw[64];
   __shared__ __align__(16) uint32_t s_lo[64];
+  pdl_trigger();
+  pdl_wait();
   const uint32_t nvb = hdr->upd_blocks;
   for (uint32_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
     const uint32_t f = owner[vb];  // the same for every thread of the block
@@ -290,6 +299,7 @@ template <bool FAST>
 __global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
 update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
                    uint32_t sweep) {
+  pdl_trigger();
   __shared__ __align__(16) uint32_t s_thr[64];
   __shared__ __align__(16) uint32_t s_alw[64];
   for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
@@ -298,6 +308,7 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
     s_alw[i] = a ? 0xFFFFFFFFu : 0u;
   }
   __syncthreads();
+  pdl_wait();  // the table above needs nothing from the previous grid
   FilmCtx c;
   c.Lx = d.Lx; c.Ly = d.Ly; c.n = d.n; c.W = d.W; c.Wp = d.Wp;
   c.y_mode = d.y_mode; c.x_pbc = d.x_pbc; c.rk0 = d.rk0; c.rk1 = d.rk1;
@@ -384,6 +395,8 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
                        const LaunchHdr* __restrict__ hdr, const uint32_t* __restrict__ pool,
                        int64_t* __restrict__ part, uint32_t done, int force) {
   __shared__ int64_t s_red[kMeasureBlock / 32];
+  pdl_trigger();
+  pdl_wait();
   const uint32_t nvb = hdr->meas_blocks;
   for (uint32_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
     const FilmDesc& F = films[owner[vb]];
@@ -418,6 +431,8 @@ measure_finalize_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restric
                         int64_t* __restrict__ direct) {
   __shared__ int64_t s_red[kMeasureBlock / 32];
   __shared__ uint32_t s_slot;
+  pdl_trigger();
+  pdl_wait();
   const uint32_t nf = hdr->n_films;
   for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
     FilmDesc& F = films[f];
@@ -452,6 +467,8 @@ measure_finalize_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restric
 }
 
 __global__ void advance_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restrict__ hdr, uint32_t n_sweeps) {
+  pdl_trigger();
+  pdl_wait();
   for (uint32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < hdr->n_films; f += gridDim.x * blockDim.x) {
     if (!films[f].active) continue;
     const uint32_t s = films[f].sweep, e = films[f].sweep_end;
@@ -476,6 +493,8 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
   __shared__ __align__(16) uint32_t s_thr[64];
   __shared__ __align__(16) uint32_t s_alw[64];
   __shared__ int64_t s_red[kResidentThreads / 32];
+  pdl_trigger();
+  pdl_wait();
   FilmDesc* Fg = films + blockIdx.x;
   {
     const uint4* src = reinterpret_cast<const uint4*>(Fg);
@@ -650,37 +669,58 @@ __global__ void unpack_kernel(FilmDesc F, const uint32_t* __restrict__ pool, int
 
 // ------------------------------------------------------ host launchers
 
+namespace {
+
+// Launch on st with programmatic stream serialisation: the kernel may begin
+// while the previous kernel of the stream is still running and orders itself
+// after it with pdl_wait.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, uint32_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace
+
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k,
                           cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  update_kernel<<<grid, kFilmThreads, 0, st>>>(L.films, L.owner_upd, L.hdr, pool, colour, k);
-  return cudaGetLastError();
+  return launch_pdl(update_kernel, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
+                    (const LaunchHdr*)L.hdr, pool, colour, k);
 }
 
 cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep,
                                cudaStream_t st) {
   const uint32_t grid = (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
   if (grid == 0) return cudaSuccess;
-  if (d.has_never) update_film_kernel<false><<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
-  else update_film_kernel<true><<<grid, kFilmThreads, 0, st>>>(d, pool, colour, sweep);
-  return cudaGetLastError();
+  if (d.has_never) return launch_pdl(update_film_kernel<false>, grid, kFilmThreads, 0, st, d, pool, colour, sweep);
+  return launch_pdl(update_film_kernel<true>, grid, kFilmThreads, 0, st, d, pool, colour, sweep);
 }
 
 cudaError_t launch_measure(const LaunchSet& L, uint32_t grid, uint32_t fin_grid, const uint32_t* pool,
                            int64_t* part, int64_t* records, uint32_t done, int force, int64_t* direct,
                            cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  measure_partial_kernel<<<grid, kMeasureBlock, 0, st>>>(L.films, L.owner_meas, L.hdr, pool, part, done, force);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(measure_partial_kernel, grid, kMeasureBlock, 0, st, (const FilmDesc*)L.films,
+                             (const uint32_t*)L.owner_meas, (const LaunchHdr*)L.hdr, pool, part, done, force);
   if (e != cudaSuccess) return e;
-  measure_finalize_kernel<<<fin_grid, kMeasureBlock, 0, st>>>(L.films, L.hdr, part, records, done, force, direct);
-  return cudaGetLastError();
+  return launch_pdl(measure_finalize_kernel, fin_grid, kMeasureBlock, 0, st, L.films, (const LaunchHdr*)L.hdr,
+                    (const int64_t*)part, records, done, force, direct);
 }
 
 cudaError_t launch_advance(const LaunchSet& L, uint32_t grid, uint32_t n_sweeps, cudaStream_t st) {
   if (grid == 0 || n_sweeps == 0) return cudaSuccess;
-  advance_kernel<<<grid, 128, 0, st>>>(L.films, L.hdr, n_sweeps);
-  return cudaGetLastError();
+  return launch_pdl(advance_kernel, grid, 128, 0, st, L.films, (const LaunchHdr*)L.hdr, n_sweeps);
 }
 
 cudaError_t launch_init(const FilmDesc& f, uint32_t* pool, int kind, uint32_t flip_lo, int flip_all,
@@ -719,9 +759,8 @@ cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_byt
   if (n_films == 0 || n_sweeps == 0) return cudaSuccess;
   if (smem_bytes > kResidentMaxSmem || threads == 0 || threads > kResidentThreads || threads % 32u)
     return cudaErrorInvalidValue;
-  if (exact) resident_kernel<false><<<n_films, threads, smem_bytes, st>>>(films, pool, records, n_sweeps);
-  else resident_kernel<true><<<n_films, threads, smem_bytes, st>>>(films, pool, records, n_sweeps);
-  return cudaGetLastError();
+  if (exact) return launch_pdl(resident_kernel<false>, n_films, threads, smem_bytes, st, films, pool, records, n_sweeps);
+  return launch_pdl(resident_kernel<true>, n_films, threads, smem_bytes, st, films, pool, records, n_sweeps);
 }
 
 int update_blocks_per_sm() {
