@@ -188,9 +188,11 @@ int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_g
   const uint32_t ug = fixed_grid ? upd_grid_max() : upd_grid();
   const uint32_t mg = fixed_grid ? meas_grid_max() : meas_grid();
   const uint32_t fg = fixed_grid ? (uint32_t)(2 * n_sm) : fin_grid();
+  bool exact = false;
+  for (const auto& d : h) exact = exact || (d.active && d.has_never);
   for (uint32_t k = k0; k < k0 + n; k++) {
-    ISG_CK(launch_update(L, ug, pool, 0, k, stream));
-    ISG_CK(launch_update(L, ug, pool, 1, k, stream));
+    ISG_CK(launch_update(L, ug, pool, 0, k, exact, stream));
+    ISG_CK(launch_update(L, ug, pool, 1, k, exact, stream));
     bool meas = all_meas;
     if (!meas)
       for (const auto& d : h)

@@ -250,14 +250,17 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 }
 
 // Half-sweep of every film of a launch: block b handles kItemsPerBlock words
-// of film owner[b], whose descriptor is staged in shared memory.
+// of film owner[b], whose descriptor is staged in shared memory.  FAST: no
+// film of the launch has a reachable thr = 0 entry (the compare-only table);
+// otherwise every film takes the exact variant.
+template <bool FAST>
 __global__ void __launch_bounds__(kFilmThreads, kMultiMinBlocks)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k) {
   constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
   static_assert(sizeof(FilmDesc) % 16 == 0, "descriptor copied as uint4");
   __shared__ __align__(16) FilmDesc s_d;
-  __shared__ __align__(16) uint32_t s_alw[64];
+  __shared__ __align__(16) uint32_t s_alw[FAST ? 1 : 64];
   __shared__ __align__(16) uint32_t s_lo[64];
   pdl_trigger();
   pdl_wait();
@@ -269,11 +272,10 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     uint4* dst = reinterpret_cast<uint4*>(&s_d);
     for (uint32_t i = threadIdx.x; i < kDescWords / 4; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    const bool fast = !s_d.has_never;
     for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
       const bool a = (s_d.always[i >> 4] >> (i & 15)) & 1u;
-      s_alw[i] = a ? 0xFFFFFFFFu : 0u;
-      s_lo[i] = fast ? (a ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
+      if (!FAST) s_alw[i] = a ? 0xFFFFFFFFu : 0u;
+      s_lo[i] = FAST ? (a ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
     }
     __syncthreads();
     if (!s_d.active || s_d.sweep + k >= s_d.sweep_end) continue;
@@ -285,10 +287,7 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     c.plane0 = pool + s_d.spin_off;
     c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
     const uint32_t first = (vb - s_d.upd_block_begin) * kItemsPerBlock;
-    if (fast)
-      sweep_block<true>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
-    else
-      sweep_block<false>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
+    sweep_block<FAST>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
   }
 }
 
@@ -692,10 +691,13 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, 
 
 }  // namespace
 
-cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k,
+cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
                           cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  return launch_pdl(update_kernel, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
+  if (exact)
+    return launch_pdl(update_kernel<false>, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films,
+                      (const uint32_t*)L.owner_upd, (const LaunchHdr*)L.hdr, pool, colour, k);
+  return launch_pdl(update_kernel<true>, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
                     (const LaunchHdr*)L.hdr, pool, colour, k);
 }
 
@@ -765,7 +767,8 @@ cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_byt
 
 int update_blocks_per_sm() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel, kFilmThreads, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<true>, kFilmThreads, 0) != cudaSuccess)
+    return 0;
   return nb;
 }
 

@@ -13,7 +13,7 @@ namespace isg {
 constexpr uint32_t kFilmThreads = 128;
 constexpr uint32_t kFilmItems = 2;
 constexpr int kFilmMinBlocks = 6;
-constexpr int kMultiMinBlocks = 5;  // the multi-film kernel carries both table paths
+constexpr int kMultiMinBlocks = 6;
 constexpr uint32_t kItemsPerBlock = kFilmThreads * kFilmItems;
 constexpr int kMeasureBlock = 256;
 
@@ -40,7 +40,8 @@ struct LaunchSet {
   LaunchHdr* hdr = nullptr;          // sizes
 };
 
-cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k,
+// exact: some film of the launch has a reachable thr = 0 entry (has_never).
+cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
                           cudaStream_t st);
 // One half-sweep of a single film whose descriptor (with `sweep` absolute) is
 // passed by value.

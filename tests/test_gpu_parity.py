@@ -143,12 +143,18 @@ def test_paper_scale_film_bit_exact():
     g.close()
 
 
-def test_mixed_batch_matches_films_run_alone():
+@pytest.mark.parametrize("cold", [False, True], ids=["fast-table", "exact-table"])
+def test_mixed_batch_matches_films_run_alone(cold):
+    """cold: one film at T -> 0 (a reachable thr = 0 entry) and one at beta = 0
+    put the whole batch on the exact-table variant of the multi-film kernel."""
     specs = []
     for i, (Lx, Ly, Lz) in enumerate([(8, 8, 8), (5, 6, 66), (3, 4, 2), (7, 5, 128), (1, 8, 16), (16, 12, 96)]):
         specs.append(dict(Lx=Lx, Ly=Ly, Lz=Lz, T=2.0 + 0.3 * i, H1=0.1 * i, seed=100 + i, replica=i,
                           measure_every=(i % 3) + 1, init_kind=ig.INIT_RANDOM if i % 2 else ig.INIT_SLAB_Y,
                           flip_p=0.02, y_mode=[ig.Y_GAPBC, ig.Y_PBC, ig.Y_APBC][i % 3]))
+    if cold:
+        specs[1]["T"] = 1e-3
+        specs[3]["T"] = math.inf
     for use_graph in (False, True):
         b = ig.Batch(specs)
         b.sweep(5, use_graph)

@@ -30,9 +30,14 @@ def _oracle(sp):
     return recs, o.get_spins()
 
 
-@pytest.mark.parametrize("budget,chunk", [(64 << 20, 16), (1 << 20, 7)])
-def test_server_jobs_match_oracle(budget, chunk):
+@pytest.mark.parametrize("budget,chunk,cold", [(64 << 20, 16, False), (1 << 20, 7, False), (64 << 20, 11, True)])
+def test_server_jobs_match_oracle(budget, chunk, cold):
+    """cold: a T -> 0 job (exact-table kernel while it is resident) and a
+    beta = 0 job in the stream."""
     specs = _specs()
+    if cold:
+        specs[3]["T"] = 1e-3
+        specs[7]["T"] = float("inf")
     srv = ig.Server(budget, chunk_sweeps=chunk)
     tickets = srv.submit(specs[:5])
     tickets += srv.submit(specs[5:])
