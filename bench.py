@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+SHAPE_NAMES = {0: "auto", 1: "resident", 2: "grid, 1 word/thread", 3: "grid, 2 words/thread"}
 METRIC = "spin-flip attempts/ns on 1 GB300, batched vs plain, % roofline; p99 latency"
 UNIT = "attempts/ns"
 SWEEPS_PER_STEP = 10
@@ -202,6 +203,7 @@ def batched_vs_plain(ig, WL, torch, sweeps=20):
         j["measure_every"] = 10
     per_sweep = sum(WL.sites(j) for j in jobs)
     b = ig.Batch(jobs)
+    shape = SHAPE_NAMES[b.autotune()]
     b.sweep(sweeps, True)  # warm-up (captures the graph)
     b.synchronize()
     t0 = time.perf_counter()
@@ -214,6 +216,7 @@ def batched_vs_plain(ig, WL, torch, sweeps=20):
     for j in jobs:
         g = ig.Film(j["Lx"], j["Ly"], j["Lz"], j["J"], j["H1"], j["T"], j["seed"], replica=j["replica"])
         g.init(j["init_kind"])
+        g.autotune(10)
         g.synchronize()
         t0 = time.perf_counter()
         g.sweep(sweeps, 10)
@@ -223,7 +226,8 @@ def batched_vs_plain(ig, WL, torch, sweeps=20):
         g.close()
     plain = per_sweep * sweeps / tp / 1e9
     return {"workload": "64 films 32x64x128..96x192x384 (16 H1 nodes x 2 T x 2 seeds), records every 10 sweeps",
-            "batched": batched, "plain": plain, "ratio": batched / plain, "unit": UNIT,
+            "batched": batched, "plain": plain, "ratio": batched / plain, "unit": UNIT, "batched_shape": shape,
+            "note": "both sides autotuned (library autotuner) before timing",
             "sweeps": {"batched": 2 * sweeps, "plain_per_film": sweeps}}
 
 
@@ -291,8 +295,8 @@ def film_8_run(ig, WL):
     grid kernels."""
     job = WL.film_8()
     out = {"workload": "8x8x8 film, 10^4 sweeps, a record every sweep"}
-    for name, path in (("resident", ig.PATH_RESIDENT), ("grid", ig.PATH_GRID)):
-        g = ig.Film(job["Lx"], job["Ly"], job["Lz"], job["J"], job["H1"], job["T"], job["seed"], path=path)
+    for name, shape in (("resident", ig.SHAPE_RESIDENT), ("grid", ig.SHAPE_GRID_1)):
+        g = ig.Film(job["Lx"], job["Ly"], job["Lz"], job["J"], job["H1"], job["T"], job["seed"], shape=shape)
         g.init(job["init_kind"])
         g.synchronize()
         t0 = time.perf_counter()
@@ -335,6 +339,7 @@ def procedures(ig, WL):
 
     def timed_run(wl):
         b = ig.Batch(wl["jobs"])
+        shape = SHAPE_NAMES[b.autotune()]
         b.synchronize()
         t0 = time.perf_counter()
         b.sweep(wl["n_sweeps"], True)
@@ -343,7 +348,8 @@ def procedures(ig, WL):
         recs = [b.read_series(i) for i in range(len(wl["jobs"]))]
         b.close()
         att = sum(WL.sites(j) for j in wl["jobs"]) * wl["n_sweeps"]
-        return recs, {"films": len(wl["jobs"]), "attempts": att, "sweep_s": dt, "attempts_per_ns": att / dt / 1e9}
+        return recs, {"films": len(wl["jobs"]), "attempts": att, "sweep_s": dt, "attempts_per_ns": att / dt / 1e9,
+                      "shape": shape}
 
     out = {}
     it = WL.interface_tension_set()
@@ -408,6 +414,10 @@ def main():
     film = ig.Film(job["Lx"], job["Ly"], job["Lz"], job["J"], job["H1"], job["T"], job["seed"],
                    replica=job["replica"], stream=stream)
     film.init(job["init_kind"], job["flip_p"])
+    # launch shapes picked by the library's autotuner (on a scratch film),
+    # for the timed steps and for the update-kernel timing pass below
+    shape_step = SHAPE_NAMES[film.autotune(SWEEPS_PER_STEP)]
+    shape_kernel = SHAPE_NAMES[film.autotune(0)]
     sites = WL.sites(job)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -498,6 +508,7 @@ def main():
                                    "free x with H1=+0.55/-0.55, periodic z, T=3, slab start + 1% flips, seed 2; "
                                    "step = 10 sweeps + one int64 record",
                        "sweeps_per_step": SWEEPS_PER_STEP, "l2": "flushed between steps (256 MiB write)",
+                       "launch_shape": {"steps": shape_step, "kernel_timing": shape_kernel},
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": per_step_launches * args.steps,
             "e2e": e2e, "cpu_baseline": cpu}

@@ -68,7 +68,18 @@ enum {
 enum { ISING_Y_GAPBC = 0, ISING_Y_PBC = 1, ISING_Y_APBC = 2 };
 enum { ISING_X_FREE = 0, ISING_X_PBC = 1 };
 enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
-enum { ISING_PATH_AUTO = 0, ISING_PATH_GRID = 1, ISING_PATH_RESIDENT = 2 };
+/* Launch shapes of the sweep (identical chains and records for every one):
+ * RESIDENT  one block keeps the whole film in shared memory for a whole
+ *           ising_sweep call (films of at most 65536 spins whose packed
+ *           planes fit in 48 KiB);
+ * GRID_1    two grid launches per sweep (plus the record kernels), one
+ *           32-site word per thread: the shortest launch latency;
+ * GRID_2    the same with two words per thread, which overlaps one word's
+ *           loads with the other's arithmetic.
+ * AUTO      the autotuner's measurement for this film shape and record
+ *           interval if there is one, else RESIDENT up to 32768 spins and
+ *           GRID_1 above. */
+enum { ISING_SHAPE_AUTO = 0, ISING_SHAPE_RESIDENT = 1, ISING_SHAPE_GRID_1 = 2, ISING_SHAPE_GRID_2 = 3 };
 
 typedef struct ising ising;
 
@@ -121,13 +132,20 @@ int ising_set_packed_device(ising *h, const uint32_t *src);
 int ising_get_sweep(const ising *h, uint64_t *sweep);
 int ising_set_sweep(ising *h, uint64_t sweep);
 
-/* Which kernels run ising_sweep (the chain and its records are identical
- * either way).  GRID: two grid-wide launches per sweep (plus the record
- * kernels), for any size.  RESIDENT: the whole call in one launch of one
- * block that keeps the packed film in shared memory, for small films (at
- * most 65536 spins whose planes fit in 48 KiB); EINVAL for a larger film.
- * AUTO (the default): RESIDENT up to 32768 spins, else GRID. */
-int ising_set_path(ising *h, int path);
+/* Pin the launch shape of this handle's ising_sweep calls (ISING_SHAPE_*;
+ * AUTO unpins).  RESIDENT on a film that does not qualify is EINVAL. */
+int ising_set_shape(ising *h, int shape);
+
+/* The shape an ising_sweep(h, n, measure_every) call would use now. */
+int ising_get_shape(ising *h, uint32_t measure_every, int *shape);
+
+/* Autotuner: times every launch shape that fits the film (a few ms per
+ * shape) on a scratch film of the same shape and parameters, with a record
+ * every measure_every sweeps, so this handle's chain is not touched.  The
+ * fastest goes into a process-wide table keyed by (Lx, Ly, Lz, boundary
+ * modes, table variant, record interval up to 16) that every AUTO handle of
+ * that key then uses; *shape (may be NULL) receives it.  Synchronises. */
+int ising_autotune(ising *h, uint32_t measure_every, int *shape);
 
 /* Enqueue n_sweeps sweeps on the handle's stream (asynchronous).  After every
  * sweep whose count of completed sweeps is a multiple of measure_every (> 0)
@@ -186,6 +204,18 @@ int ising_batch_set_stream(ising_batch *b, void *cuda_stream);
  * job's measure_every.  use_graph != 0 captures the sweep chunk in a CUDA
  * graph once and replays it. */
 int ising_batch_sweep(ising_batch *b, uint64_t n_sweeps, int use_graph);
+
+/* Launch shape of the batch's grid kernels: GRID_1, GRID_2, or AUTO (the
+ * autotuner's choice once ising_batch_autotune has run, else GRID_1).
+ * RESIDENT is EINVAL for a batch.  Changing it drops the captured graphs. */
+int ising_batch_set_shape(ising_batch *b, int shape);
+int ising_batch_get_shape(ising_batch *b, int *shape);
+
+/* Autotuner: times GRID_1 and GRID_2 on a scratch batch of the same jobs
+ * (from their initial states; the kernels' work does not depend on the
+ * spins), graph replay and records included, and adopts the faster unless
+ * a shape is pinned; *shape (may be NULL) receives it.  Synchronises. */
+int ising_batch_autotune(ising_batch *b, int *shape);
 
 /* Per-film accessors (index i < n).  Host buffers; synchronise. */
 int ising_batch_get_spins(ising_batch *b, size_t i, int8_t *s);

@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = range(7)
 Y_GAPBC, Y_PBC, Y_APBC = 0, 1, 2
 X_FREE, X_PBC = 0, 1
 INIT_RANDOM, INIT_SLAB_Y, INIT_ALL_UP = 0, 1, 2
-PATH_AUTO, PATH_GRID, PATH_RESIDENT = 0, 1, 2
+SHAPE_AUTO, SHAPE_RESIDENT, SHAPE_GRID_1, SHAPE_GRID_2 = 0, 1, 2, 3
 
 _c = ctypes
 P = _c.c_void_p
@@ -57,7 +57,12 @@ _SIGS = {
     "ising_create": [_c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double, _c.c_uint64,
                      _c.POINTER(P)],
     "ising_set_options": [P, _c.c_int, _c.c_int, _c.c_double, _c.c_uint32],
-    "ising_set_path": [P, _c.c_int],
+    "ising_set_shape": [P, _c.c_int],
+    "ising_get_shape": [P, _c.c_uint32, _c.POINTER(_c.c_int)],
+    "ising_autotune": [P, _c.c_uint32, _c.POINTER(_c.c_int)],
+    "ising_batch_set_shape": [P, _c.c_int],
+    "ising_batch_get_shape": [P, _c.POINTER(_c.c_int)],
+    "ising_batch_autotune": [P, _c.POINTER(_c.c_int)],
     "ising_set_params": [P, _c.c_double, _c.c_double, _c.c_double],
     "ising_set_stream": [P, P],
     "ising_init": [P, _c.c_int, _c.c_double],
@@ -164,7 +169,7 @@ class Film:
     """One film (``ising_create`` ... ``ising_destroy``)."""
 
     def __init__(self, Lx, Ly, Lz, J=1.0, H1=0.0, T=3.0, seed=1, *, y_mode=Y_GAPBC, x_mode=X_FREE, H=0.0,
-                 replica=0, stream=None, path=PATH_AUTO):
+                 replica=0, stream=None, shape=SHAPE_AUTO):
         self.Lx, self.Ly, self.Lz = int(Lx), int(Ly), int(Lz)
         self.J, self.H1, self.T, self.H = float(J), float(H1), float(T), float(H)
         h = P()
@@ -174,11 +179,22 @@ class Film:
         check(lib().ising_set_options(h, int(y_mode), int(x_mode), self.H, int(replica)), "ising_set_options")
         if stream is not None:
             check(lib().ising_set_stream(h, _torch_stream(stream)), "ising_set_stream")
-        if path != PATH_AUTO:
-            self.set_path(path)
+        if shape != SHAPE_AUTO:
+            self.set_shape(shape)
 
-    def set_path(self, path):
-        check(lib().ising_set_path(self._h, int(path)), "ising_set_path")
+    def set_shape(self, shape):
+        check(lib().ising_set_shape(self._h, int(shape)), "ising_set_shape")
+
+    def get_shape(self, measure_every):
+        v = _c.c_int()
+        check(lib().ising_get_shape(self._h, int(measure_every), _c.byref(v)), "ising_get_shape")
+        return v.value
+
+    def autotune(self, measure_every):
+        """Time every launch shape on a scratch film; returns the fastest."""
+        v = _c.c_int()
+        check(lib().ising_autotune(self._h, int(measure_every), _c.byref(v)), "ising_autotune")
+        return v.value
 
     def close(self):
         if getattr(self, "_h", None):
@@ -314,6 +330,20 @@ class Batch:
 
     def sweep(self, n, use_graph=False):
         check(lib().ising_batch_sweep(self._h, int(n), 1 if use_graph else 0), "ising_batch_sweep")
+
+    def set_shape(self, shape):
+        check(lib().ising_batch_set_shape(self._h, int(shape)), "ising_batch_set_shape")
+
+    def get_shape(self):
+        v = _c.c_int()
+        check(lib().ising_batch_get_shape(self._h, _c.byref(v)), "ising_batch_get_shape")
+        return v.value
+
+    def autotune(self):
+        """Time GRID_1 and GRID_2 on a scratch batch; adopts and returns the faster."""
+        v = _c.c_int()
+        check(lib().ising_batch_autotune(self._h, _c.byref(v)), "ising_batch_autotune")
+        return v.value
 
     def get_spins(self, i):
         s = self.specs[i]

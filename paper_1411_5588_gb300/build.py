@@ -22,7 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libising_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ising_kernels.cu", "ising_api.cpp", "ising_batch.cpp", "ising_server.cpp", "ising_ti.cpp",
-           "ising_noalloc.cu", "ising_analysis.cpp"]
+           "ising_noalloc.cu", "ising_analysis.cpp", "ising_tune.cpp"]
 
 
 def nvcc() -> str:

@@ -137,7 +137,7 @@ void FilmSet::layout(bool assign_part) {
     d.upd_block_begin = ub;
     d.meas_block_begin = mb;
     if (assign_part) d.part_off = po;
-    ub += (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
+    ub += (d.upd_items + items_per_block(items) - 1) / items_per_block(items);
     mb += d.Lx * d.meas_bpl;
     po += part_len(d);
   }
@@ -167,7 +167,7 @@ int FilmSet::upload() {
   uint32_t* om = ou + hh.upd_blocks;
   for (size_t f = 0; f < nf; f++) {
     const FilmDesc& d = h[f];
-    const uint32_t nb = (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
+    const uint32_t nb = (d.upd_items + items_per_block(items) - 1) / items_per_block(items);
     for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
     for (uint32_t b = 0; b < d.Lx * d.meas_bpl; b++) om[d.meas_block_begin + b] = (uint32_t)f;
   }
@@ -191,8 +191,8 @@ int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_g
   bool exact = false;
   for (const auto& d : h) exact = exact || (d.active && d.has_never);
   for (uint32_t k = k0; k < k0 + n; k++) {
-    ISG_CK(launch_update(L, ug, pool, 0, k, exact, stream));
-    ISG_CK(launch_update(L, ug, pool, 1, k, exact, stream));
+    ISG_CK(launch_update(L, ug, pool, 0, k, exact, items, stream));
+    ISG_CK(launch_update(L, ug, pool, 1, k, exact, items, stream));
     bool meas = all_meas;
     if (!meas)
       for (const auto& d : h)
@@ -250,7 +250,7 @@ struct ising {
   int64_t* d_direct = nullptr;
   int8_t* d_stage = nullptr;
   bool dirty = true;
-  int path = ISING_PATH_AUTO;
+  int shape = ISING_SHAPE_AUTO;
   FilmDesc& d() { return fs.h[0]; }
 };
 
@@ -259,6 +259,18 @@ namespace {
 int ensure_stage(ising* h) {
   if (!h->d_stage) ISG_CK(cudaMalloc(&h->d_stage, (size_t)h->d().Lx * h->d().Ly * h->d().Lz));
   return ISING_OK;
+}
+
+// The launch shape of an ising_sweep call: the pinned one, else the
+// autotuner's choice for this film shape and record interval, else the
+// resident kernel up to kResidentAutoSites spins and one word per thread above.
+int resolve_shape(ising* h, uint32_t measure_every) {
+  const FilmDesc& d = h->d();
+  if (h->shape != ISING_SHAPE_AUTO) return h->shape;
+  int s = 0;
+  if (tune_lookup(tune_key(d, measure_every), &s) && (s != ISING_SHAPE_RESIDENT || resident_smem_bytes(d))) return s;
+  const uint64_t sites = (uint64_t)d.Lx * d.Ly * d.Lz;
+  return (sites <= kResidentAutoSites && resident_smem_bytes(d)) ? ISING_SHAPE_RESIDENT : ISING_SHAPE_GRID_1;
 }
 
 int sync_desc(ising* h) {
@@ -479,14 +491,69 @@ int ising_set_sweep(ising* h, uint64_t sweep) {
   return sync_desc(h);
 }
 
-int ising_set_path(ising* h, int path) {
+int ising_set_shape(ising* h, int shape) {
   clear_error();
   if (!h) return fail(ISING_EINVAL, "NULL handle");
-  if (path != ISING_PATH_AUTO && path != ISING_PATH_GRID && path != ISING_PATH_RESIDENT)
-    return fail(ISING_EINVAL, "unknown path %d", path);
-  if (path == ISING_PATH_RESIDENT && !resident_smem_bytes(h->d()))
-    return fail(ISING_EINVAL, "film too large for the resident path");
-  h->path = path;
+  if (shape < ISING_SHAPE_AUTO || shape > ISING_SHAPE_GRID_2) return fail(ISING_EINVAL, "unknown shape %d", shape);
+  if (shape == ISING_SHAPE_RESIDENT && !resident_smem_bytes(h->d()))
+    return fail(ISING_EINVAL, "film too large for the resident kernel");
+  h->shape = shape;
+  return ISING_OK;
+}
+
+int ising_get_shape(ising* h, uint32_t measure_every, int* shape) {
+  clear_error();
+  if (!h || !shape) return fail(ISING_EINVAL, "NULL argument");
+  *shape = resolve_shape(h, measure_every);
+  return ISING_OK;
+}
+
+int ising_autotune(ising* h, uint32_t measure_every, int* shape) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  const FilmDesc& d = h->d();
+  // a scratch film of the same shape and parameters: the kernels do the same
+  // work whatever the spins are, and the handle's own chain is not touched
+  ising* s = nullptr;
+  int rc = ising_create(d.Lx, d.Ly, d.Lz, h->J, h->H1, h->T, h->seed, &s);
+  if (rc) return rc;
+  rc = ising_set_options(s, h->y_mode, h->x_mode, h->H, h->replica);
+  if (!rc) rc = ising_init(s, ISING_INIT_RANDOM, 0.0);
+  const double sites = (double)d.Lx * d.Ly * d.Lz;
+  const uint64_t n = (uint64_t)std::min(400.0, std::max(4.0, std::round(4e8 / sites)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(ISING_ECUDA, "event creation failed");
+  int best = ISING_SHAPE_GRID_1;
+  float best_ms = 3.0e38f;
+  std::vector<int64_t> drain;
+  for (int cand = ISING_SHAPE_RESIDENT; !rc && cand <= ISING_SHAPE_GRID_2; cand++) {
+    if (cand == ISING_SHAPE_RESIDENT && !resident_smem_bytes(d)) continue;
+    s->shape = cand;
+    float ms = 3.0e38f;
+    for (int rep = 0; !rc && rep < 3; rep++) {  // the first run warms up
+      if (cudaEventRecord(e0, s->fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
+      if (!rc) rc = ising_sweep(s, n, measure_every);
+      if (!rc && cudaEventRecord(e1, s->fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
+      if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ISING_ECUDA, "event wait failed");
+      float t = 0.f;
+      if (!rc && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = fail(ISING_ECUDA, "event time failed");
+      if (!rc && rep > 0) ms = std::min(ms, t);
+      drain.resize((size_t)(s->rec_written - s->rec_read) * record_len(s->d()) + 1);
+      size_t got = 0;
+      if (!rc) rc = ising_read_series(s, drain.data(), (size_t)(s->rec_written - s->rec_read), &got);
+    }
+    if (!rc && ms < best_ms) {
+      best_ms = ms;
+      best = cand;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  ising_destroy(s);
+  if (rc) return rc;
+  tune_store(tune_key(d, measure_every), best);
+  if (shape) *shape = best;
   return ISING_OK;
 }
 
@@ -506,10 +573,9 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
   if (rc) return rc;
   rc = sync_desc(h);
   if (rc) return rc;
-  const bool auto_ok = (uint64_t)d.Lx * d.Ly * d.Lz <= kResidentAutoSites;
-  const uint32_t smem = (h->path == ISING_PATH_RESIDENT || (h->path == ISING_PATH_AUTO && auto_ok))
-                            ? resident_smem_bytes(d) : 0u;
-  if (smem) {
+  const int shape = resolve_shape(h, measure_every);
+  if (shape == ISING_SHAPE_RESIDENT) {
+    const uint32_t smem = resident_smem_bytes(d);
     // small film: every sweep of the call in one launch, planes in shared memory
     ISG_CK(launch_resident(h->fs.L.films, 1, smem, resident_threads(d), d.has_never != 0, h->fs.pool, h->fs.rec,
                            (uint32_t)n, h->fs.stream));
@@ -519,10 +585,11 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
     return ISING_OK;
   }
   // single film: the descriptor travels as a kernel parameter
+  const uint32_t items = shape == ISING_SHAPE_GRID_2 ? 2u : 1u;
   for (uint64_t k = 0; k < n; k++) {
     const uint32_t t = (uint32_t)(s0 + k);
-    ISG_CK(launch_update_film(d, h->fs.pool, 0, t, h->fs.stream));
-    ISG_CK(launch_update_film(d, h->fs.pool, 1, t, h->fs.stream));
+    ISG_CK(launch_update_film(d, h->fs.pool, 0, t, items, h->fs.stream));
+    ISG_CK(launch_update_film(d, h->fs.pool, 1, t, items, h->fs.stream));
     if (measure_every && (s0 + k + 1) % measure_every == 0)
       ISG_CK(launch_measure(h->fs.L, h->fs.meas_grid(), 1, h->fs.pool, h->fs.part, h->fs.rec, (uint32_t)(k + 1), 0,
                             nullptr, h->fs.stream));

@@ -24,6 +24,8 @@ struct ising_batch {
   int8_t* d_stage = nullptr;
   size_t stage_bytes = 0;
   bool dirty = true;
+  int shape = ISING_SHAPE_AUTO;  // pinned launch shape, or AUTO
+  uint32_t tuned_items = 0;      // ising_batch_autotune's choice (0: none yet)
   std::map<uint32_t, cudaGraphExec_t> graphs;  // chunk length -> executable graph
 
   void drop_graphs() {
@@ -93,6 +95,18 @@ int batch_ensure_rings(ising_batch* b, const std::vector<uint64_t>& extra) {
 }
 
 uint64_t lcm_u64(uint64_t a, uint64_t b) { return a / std::gcd(a, b) * b; }
+
+// Switch the grid kernels' words per thread: new block ranges and owner
+// tables, and the captured graphs (which bake in the old ones) are dropped.
+int apply_items(ising_batch* b, uint32_t items) {
+  if (b->fs.items == items) return ISING_OK;
+  ISG_CK(cudaStreamSynchronize(b->fs.stream));
+  b->fs.items = items;
+  b->fs.layout();
+  b->dirty = true;
+  b->drop_graphs();
+  return ISING_OK;
+}
 
 int direct_sweeps(ising_batch* b, uint32_t n) {
   if (n == 0) return ISING_OK;
@@ -248,6 +262,69 @@ int ising_batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
     b->rec_written[f] += extra[f];
   }
   return ISING_OK;
+}
+
+int ising_batch_set_shape(ising_batch* b, int shape) {
+  clear_error();
+  if (!b) return fail(ISING_EINVAL, "NULL batch");
+  if (shape != ISING_SHAPE_AUTO && shape != ISING_SHAPE_GRID_1 && shape != ISING_SHAPE_GRID_2)
+    return fail(ISING_EINVAL, "batches take AUTO, GRID_1 or GRID_2");
+  b->shape = shape;
+  const uint32_t items = shape == ISING_SHAPE_GRID_2 ? 2u
+                         : shape == ISING_SHAPE_GRID_1 ? 1u
+                                                       : (b->tuned_items ? b->tuned_items : 1u);
+  return apply_items(b, items);
+}
+
+int ising_batch_get_shape(ising_batch* b, int* shape) {
+  clear_error();
+  if (!b || !shape) return fail(ISING_EINVAL, "NULL argument");
+  *shape = b->fs.items == 2 ? ISING_SHAPE_GRID_2 : ISING_SHAPE_GRID_1;
+  return ISING_OK;
+}
+
+int ising_batch_autotune(ising_batch* b, int* shape) {
+  clear_error();
+  if (!b) return fail(ISING_EINVAL, "NULL batch");
+  // a scratch batch of the same films from their initial states: the kernels
+  // do the same work whatever the spins are, and this batch is not touched
+  ising_batch* s = nullptr;
+  int rc = ising_batch_create(b->jobs.data(), b->jobs.size(), &s);
+  if (rc) return rc;
+  double sites = 0;
+  for (const auto& d : b->fs.h) sites += (double)d.Lx * d.Ly * d.Lz;
+  const uint64_t n = (uint64_t)std::min(1024.0, std::max(64.0, std::round(4e8 / sites)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = fail(ISING_ECUDA, "event creation failed");
+  uint32_t best = 1;
+  float best_ms = 3.0e38f;
+  for (uint32_t items = 1; !rc && items <= kMaxFilmItems; items++) {
+    rc = apply_items(s, items);
+    float ms = 3.0e38f;
+    for (int rep = 0; !rc && rep < 3; rep++) {  // the first run captures the graph
+      if (cudaEventRecord(e0, s->fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
+      if (!rc) rc = ising_batch_sweep(s, n, 1);
+      if (!rc && cudaEventRecord(e1, s->fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
+      if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ISING_ECUDA, "event wait failed");
+      float t = 0.f;
+      if (!rc && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = fail(ISING_ECUDA, "event time failed");
+      if (!rc && rep > 0) ms = std::min(ms, t);
+      for (size_t f = 0; f < s->fs.h.size(); f++) s->rec_read[f] = s->rec_written[f];  // drop the records
+    }
+    if (!rc && ms < best_ms) {
+      best_ms = ms;
+      best = items;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  ising_batch_destroy(s);
+  if (rc) return rc;
+  b->tuned_items = best;
+  if (b->shape == ISING_SHAPE_AUTO) rc = apply_items(b, best);
+  if (!rc && shape) *shape = best == 2 ? ISING_SHAPE_GRID_2 : ISING_SHAPE_GRID_1;
+  return rc;
 }
 
 int ising_batch_get_spins(ising_batch* b, size_t i, int8_t* s) {

@@ -47,6 +47,7 @@ struct FilmSet {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int n_sm = 0, upd_per_sm = 0, meas_per_sm = 0;
+  uint32_t items = 1;  // words per thread of the grid update kernel (1 or 2)
 
   std::vector<FilmDesc> h;  // host mirror (counters tracked on the host too)
   LaunchHdr hh{};
@@ -77,5 +78,16 @@ struct FilmSet {
   int release();
   ~FilmSet() { release(); }
 };
+
+// Autotuner cache, shared by every handle of the process: the fastest launch
+// shape (ISING_SHAPE_*) measured for a film shape, boundary, table variant
+// and record interval.
+struct TuneKey {
+  uint32_t Lx, Ly, Lz, y_mode, x_pbc, exact, m_class;
+  bool operator<(const TuneKey& o) const;
+};
+TuneKey tune_key(const FilmDesc& d, uint32_t measure_every);
+bool tune_lookup(const TuneKey& k, int* shape);
+void tune_store(const TuneKey& k, int shape);
 
 }  // namespace isg

@@ -226,16 +226,16 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
 
 }  // namespace
 
-// The words of one block of kItemsPerBlock consecutive words: each thread
-// fetches its kFilmItems words (kFilmThreads apart) before deciding any.
-template <bool FAST>
+// The words of one block of ITEMS * kFilmThreads consecutive words: each
+// thread fetches its ITEMS words (kFilmThreads apart) before deciding any.
+template <bool FAST, uint32_t ITEMS>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw) {
-  Fetched fw[kFilmItems];
-  bool mine[kFilmItems];
+  Fetched fw[ITEMS];
+  bool mine[ITEMS];
 #pragma unroll
-  for (uint32_t it = 0; it < kFilmItems; it++) {
+  for (uint32_t it = 0; it < ITEMS; it++) {
     const uint32_t item = first + threadIdx.x + it * kFilmThreads;
     mine[it] = item < items;
     if (mine[it]) {
@@ -245,15 +245,15 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
     }
   }
 #pragma unroll
-  for (uint32_t it = 0; it < kFilmItems; it++)
+  for (uint32_t it = 0; it < ITEMS; it++)
     if (mine[it]) update_fetched<FAST>(c, fw[it], s_thr, s_alw);
 }
 
-// Half-sweep of every film of a launch: block b handles kItemsPerBlock words
-// of film owner[b], whose descriptor is staged in shared memory.  FAST: no
-// film of the launch has a reachable thr = 0 entry (the compare-only table);
-// otherwise every film takes the exact variant.
-template <bool FAST>
+// Half-sweep of every film of a launch: block b handles ITEMS * kFilmThreads
+// words of film owner[b], whose descriptor is staged in shared memory.  FAST:
+// no film of the launch has a reachable thr = 0 entry (the compare-only
+// table); otherwise every film takes the exact variant.
+template <bool FAST, uint32_t ITEMS>
 __global__ void __launch_bounds__(kFilmThreads, kMultiMinBlocks)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k) {
@@ -286,15 +286,16 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     c.colour = colour; c.sweep = s_d.sweep + k;
     c.plane0 = pool + s_d.spin_off;
     c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
-    const uint32_t first = (vb - s_d.upd_block_begin) * kItemsPerBlock;
-    sweep_block<FAST>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
+    const uint32_t first = (vb - s_d.upd_block_begin) * (ITEMS * kFilmThreads);
+    sweep_block<FAST, ITEMS>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
   }
 }
 
 // Single-film half-sweep.  The descriptor is a __grid_constant__ kernel
 // parameter, so every per-film constant (round keys included) is read straight
-// from the constant bank; block b updates words b*kItemsPerBlock onwards.
-template <bool FAST>
+// from the constant bank; block b updates words b * ITEMS * kFilmThreads
+// onwards.
+template <bool FAST, uint32_t ITEMS>
 __global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
 update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
                    uint32_t sweep) {
@@ -315,7 +316,7 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   c.colour = colour; c.sweep = sweep;
   c.plane0 = pool + d.spin_off;
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
-  sweep_block<FAST>(c, blockIdx.x * kItemsPerBlock, d.upd_items, d.divw_m, d.divw_l, d.divy_m, d.divy_l, s_thr,
+  sweep_block<FAST, ITEMS>(c, blockIdx.x * (ITEMS * kFilmThreads), d.upd_items, d.divw_m, d.divw_l, d.divy_m, d.divy_l, s_thr,
                     s_alw);
 }
 
@@ -692,21 +693,22 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, 
 }  // namespace
 
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          cudaStream_t st) {
+                          uint32_t items, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  if (exact)
-    return launch_pdl(update_kernel<false>, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films,
-                      (const uint32_t*)L.owner_upd, (const LaunchHdr*)L.hdr, pool, colour, k);
-  return launch_pdl(update_kernel<true>, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
+  auto* kern = exact ? (items == 2 ? update_kernel<false, 2> : update_kernel<false, 1>)
+                     : (items == 2 ? update_kernel<true, 2> : update_kernel<true, 1>);
+  return launch_pdl(kern, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
                     (const LaunchHdr*)L.hdr, pool, colour, k);
 }
 
-cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep,
+cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep, uint32_t items,
                                cudaStream_t st) {
-  const uint32_t grid = (d.upd_items + kItemsPerBlock - 1) / kItemsPerBlock;
+  const uint32_t ipb = items_per_block(items);
+  const uint32_t grid = (d.upd_items + ipb - 1) / ipb;
   if (grid == 0) return cudaSuccess;
-  if (d.has_never) return launch_pdl(update_film_kernel<false>, grid, kFilmThreads, 0, st, d, pool, colour, sweep);
-  return launch_pdl(update_film_kernel<true>, grid, kFilmThreads, 0, st, d, pool, colour, sweep);
+  auto* kern = d.has_never ? (items == 2 ? update_film_kernel<false, 2> : update_film_kernel<false, 1>)
+                           : (items == 2 ? update_film_kernel<true, 2> : update_film_kernel<true, 1>);
+  return launch_pdl(kern, grid, kFilmThreads, 0, st, d, pool, colour, sweep);
 }
 
 cudaError_t launch_measure(const LaunchSet& L, uint32_t grid, uint32_t fin_grid, const uint32_t* pool,
@@ -767,7 +769,7 @@ cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_byt
 
 int update_blocks_per_sm() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<true>, kFilmThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<true, 1>, kFilmThreads, 0) != cudaSuccess)
     return 0;
   return nb;
 }

@@ -8,13 +8,17 @@
 
 namespace isg {
 
-// Update kernels: threads per block, words per thread, blocks per SM; one
-// block updates kItemsPerBlock consecutive words of one film.
+// Grid update kernels: threads per block and blocks per SM.  A block updates
+// items * kFilmThreads consecutive words of one film, items (words per
+// thread, 1 or 2) being the launch shape the autotuner picks per film or
+// film set: one word per thread halves the dependency chain of a launch
+// (small and medium films are latency bound), two let each thread overlap
+// the loads of its second word with the first word's arithmetic.
 constexpr uint32_t kFilmThreads = 128;
-constexpr uint32_t kFilmItems = 2;
+constexpr uint32_t kMaxFilmItems = 2;
 constexpr int kFilmMinBlocks = 6;
 constexpr int kMultiMinBlocks = 6;
-constexpr uint32_t kItemsPerBlock = kFilmThreads * kFilmItems;
+inline uint32_t items_per_block(uint32_t items) { return kFilmThreads * items; }
 constexpr int kMeasureBlock = 256;
 
 // Items a measurement block covers per layer before another block is added.
@@ -40,12 +44,13 @@ struct LaunchSet {
   LaunchHdr* hdr = nullptr;          // sizes
 };
 
-// exact: some film of the launch has a reachable thr = 0 entry (has_never).
+// exact: some film of the launch has a reachable thr = 0 entry (has_never);
+// items: words per thread (1 or 2), matching the owner table's block size.
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          cudaStream_t st);
+                          uint32_t items, cudaStream_t st);
 // One half-sweep of a single film whose descriptor (with `sweep` absolute) is
 // passed by value.
-cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep,
+cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep, uint32_t items,
                                cudaStream_t st);
 cudaError_t launch_measure(const LaunchSet& L, uint32_t grid, uint32_t fin_grid, const uint32_t* pool,
                            int64_t* part, int64_t* records, uint32_t done, int force, int64_t* direct,

@@ -38,21 +38,24 @@ CASES = [
 ]
 
 
-def _pair(case, seed=7, replica=3, path=ig.PATH_AUTO):
+def _pair(case, seed=7, replica=3, shape=ig.SHAPE_AUTO):
     Lx, Ly, Lz, ym, xm, H1, H, T, kind, flip = case
-    g = ig.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica, path=path)
+    g = ig.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica, shape=shape)
     o = O.Film(Lx, Ly, Lz, 1.0, H1, T, seed, y_mode=ym, x_mode=xm, H=H, replica=replica)
     g.init(kind, flip)
     o.init(kind, flip)
     return g, o
 
 
-@pytest.mark.parametrize("path", [ig.PATH_GRID, ig.PATH_RESIDENT], ids=["grid", "resident"])
+SHAPES = [ig.SHAPE_RESIDENT, ig.SHAPE_GRID_1, ig.SHAPE_GRID_2]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2"])
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-y{c[3]}x{c[4]}-T{c[7]}" for c in CASES])
-def test_sweeps_bit_exact(case, path):
-    """Both single-film paths: the grid kernels (two launches per sweep) and
-    the resident kernel (the film in shared memory for the whole call)."""
-    g, o = _pair(case, path=path)
+def test_sweeps_bit_exact(case, shape):
+    """Every launch shape: the resident kernel (the film in shared memory for
+    the whole call) and the grid kernels with one or two words per thread."""
+    g, o = _pair(case, shape=shape)
     assert np.array_equal(g.get_spins(), o.get_spins()), "initial state differs"
     done = 0
     for n, m in ((1, 1), (1, 1), (8, 2), (90, 3)):
@@ -143,8 +146,9 @@ def test_paper_scale_film_bit_exact():
     g.close()
 
 
+@pytest.mark.parametrize("shape", [ig.SHAPE_GRID_1, ig.SHAPE_GRID_2], ids=["grid1", "grid2"])
 @pytest.mark.parametrize("cold", [False, True], ids=["fast-table", "exact-table"])
-def test_mixed_batch_matches_films_run_alone(cold):
+def test_mixed_batch_matches_films_run_alone(cold, shape):
     """cold: one film at T -> 0 (a reachable thr = 0 entry) and one at beta = 0
     put the whole batch on the exact-table variant of the multi-film kernel."""
     specs = []
@@ -157,6 +161,7 @@ def test_mixed_batch_matches_films_run_alone(cold):
         specs[3]["T"] = math.inf
     for use_graph in (False, True):
         b = ig.Batch(specs)
+        b.set_shape(shape)
         b.sweep(5, use_graph)
         b.sweep(91, use_graph)
         for i, sp in enumerate(specs):
@@ -197,19 +202,60 @@ def test_thermodynamic_integration_from_gpu_records_matches_oracle():
     b.close()
 
 
-def test_resident_path_limits():
-    """AUTO picks the resident kernel only for films it can hold; forcing it
-    on a larger film is refused, and a film can switch paths mid-chain."""
+def test_shape_limits_and_switches():
+    """The resident kernel is refused for a film it cannot hold; a film can
+    change launch shape in the middle of its chain."""
     big = ig.Film(64, 64, 32, 1.0, 0.5, 3.0, 1)  # 131072 spins
     with pytest.raises(ig.IsingError) as e:
-        big.set_path(ig.PATH_RESIDENT)
+        big.set_shape(ig.SHAPE_RESIDENT)
     assert e.value.status == ig.EINVAL
+    assert big.get_shape(1) in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2)
     big.close()
     case = (12, 10, 40, ig.Y_GAPBC, ig.X_FREE, 0.55, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01)
     g, o = _pair(case)
-    for path, n, m in ((ig.PATH_RESIDENT, 7, 2), (ig.PATH_GRID, 5, 3), (ig.PATH_RESIDENT, 11, 1)):
-        g.set_path(path)
+    for shape, n, m in ((ig.SHAPE_RESIDENT, 7, 2), (ig.SHAPE_GRID_2, 5, 3), (ig.SHAPE_GRID_1, 4, 4),
+                        (ig.SHAPE_RESIDENT, 11, 1)):
+        g.set_shape(shape)
         g.sweep(n, m)
         assert np.array_equal(g.read_series(), o.sweep(n, m))
         assert np.array_equal(g.get_spins(), o.get_spins())
     g.close()
+
+
+def test_autotune_leaves_the_chain_alone():
+    """ising_autotune runs on a scratch film: the tuned film's chain is still
+    the oracle's, the choice is a valid shape, and another AUTO film of the
+    same shape and record interval picks it up from the process table."""
+    case = (20, 24, 40, ig.Y_GAPBC, ig.X_FREE, 0.45, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01)
+    g, o = _pair(case)
+    g.sweep(3, 1)
+    want = [o.sweep(3, 1)]
+    best = g.autotune(1)
+    assert best in SHAPES
+    g.sweep(9, 1)
+    want.append(o.sweep(9, 1))
+    assert np.array_equal(g.read_series(), np.concatenate(want))
+    assert np.array_equal(g.get_spins(), o.get_spins())
+    g.close()
+    g, o = _pair(case)
+    assert g.get_shape(1) == best
+    g.sweep(12, 1)
+    assert np.array_equal(g.read_series(), o.sweep(12, 1))
+    assert np.array_equal(g.get_spins(), o.get_spins())
+    g.close()
+
+
+def test_batch_autotune_leaves_the_chains_alone():
+    specs = [dict(Lx=Lx, Ly=Ly, Lz=Lz, T=3.0, H1=0.3, seed=9, replica=i, measure_every=2,
+                  init_kind=ig.INIT_SLAB_Y, flip_p=0.02) for i, (Lx, Ly, Lz) in enumerate([(8, 16, 32), (12, 20, 64)])]
+    b = ig.Batch(specs)
+    b.sweep(4, True)
+    best = b.autotune()
+    assert best in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2) and b.get_shape() == best
+    b.sweep(40, True)
+    for i, sp in enumerate(specs):
+        o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], replica=sp["replica"])
+        o.init(sp["init_kind"], sp["flip_p"])
+        assert np.array_equal(b.read_series(i), o.sweep(44, 2))
+        assert np.array_equal(b.get_spins(i), o.get_spins())
+    b.close()
