@@ -204,6 +204,7 @@ def batched_vs_plain(ig, WL, torch, sweeps=20):
     per_sweep = sum(WL.sites(j) for j in jobs)
     b = ig.Batch(jobs)
     shape = SHAPE_NAMES[b.autotune()]
+    b.reserve_records(2 * sweeps)
     b.sweep(sweeps, True)  # warm-up (captures the graph)
     b.synchronize()
     t0 = time.perf_counter()
@@ -340,6 +341,7 @@ def procedures(ig, WL):
     def timed_run(wl):
         b = ig.Batch(wl["jobs"])
         shape = SHAPE_NAMES[b.autotune()]
+        b.reserve_records(wl["n_sweeps"])  # records every sweep: no ring growth while timed
         b.synchronize()
         t0 = time.perf_counter()
         b.sweep(wl["n_sweeps"], True)
@@ -426,6 +428,7 @@ def main():
             film.sweep(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
         film.synchronize()
         film.read_series()
+        film.reserve_records(args.steps)  # no series growth inside the timed steps
         events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(args.steps)]
         sampler = ClockSampler(torch.cuda.current_device())

@@ -132,6 +132,11 @@ int ising_set_packed_device(ising *h, const uint32_t *src);
 int ising_get_sweep(const ising *h, uint64_t *sweep);
 int ising_set_sweep(ising *h, uint64_t sweep);
 
+/* Make room for n_records more pending records, so that later ising_sweep
+ * calls do not grow the series (growth is a device allocation, a copy of the
+ * pending records and a synchronisation).  ENOMEM. */
+int ising_reserve_records(ising *h, uint64_t n_records);
+
 /* Pin the launch shape of this handle's ising_sweep calls (ISING_SHAPE_*;
  * AUTO unpins).  RESIDENT on a film that does not qualify is EINVAL. */
 int ising_set_shape(ising *h, int shape);
@@ -204,6 +209,10 @@ int ising_batch_set_stream(ising_batch *b, void *cuda_stream);
  * job's measure_every.  use_graph != 0 captures the sweep chunk in a CUDA
  * graph once and replays it. */
 int ising_batch_sweep(ising_batch *b, uint64_t n_sweeps, int use_graph);
+
+/* Room for n_records more pending records of every film that records (see
+ * ising_reserve_records).  ENOMEM. */
+int ising_batch_reserve_records(ising_batch *b, uint64_t n_records);
 
 /* Launch shape of the batch's grid kernels: GRID_1, GRID_2, or AUTO (the
  * autotuner's choice once ising_batch_autotune has run, else GRID_1).

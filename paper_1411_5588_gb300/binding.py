@@ -58,6 +58,8 @@ _SIGS = {
                      _c.POINTER(P)],
     "ising_set_options": [P, _c.c_int, _c.c_int, _c.c_double, _c.c_uint32],
     "ising_set_shape": [P, _c.c_int],
+    "ising_reserve_records": [P, _c.c_uint64],
+    "ising_batch_reserve_records": [P, _c.c_uint64],
     "ising_get_shape": [P, _c.c_uint32, _c.POINTER(_c.c_int)],
     "ising_autotune": [P, _c.c_uint32, _c.POINTER(_c.c_int)],
     "ising_batch_set_shape": [P, _c.c_int],
@@ -184,6 +186,9 @@ class Film:
 
     def set_shape(self, shape):
         check(lib().ising_set_shape(self._h, int(shape)), "ising_set_shape")
+
+    def reserve_records(self, n):
+        check(lib().ising_reserve_records(self._h, int(n)), "ising_reserve_records")
 
     def get_shape(self, measure_every):
         v = _c.c_int()
@@ -333,6 +338,9 @@ class Batch:
 
     def set_shape(self, shape):
         check(lib().ising_batch_set_shape(self._h, int(shape)), "ising_batch_set_shape")
+
+    def reserve_records(self, n):
+        check(lib().ising_batch_reserve_records(self._h, int(n)), "ising_batch_reserve_records")
 
     def get_shape(self):
         v = _c.c_int()

@@ -71,6 +71,9 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   }
   d.upd_items = d.Lx * (d.Ly - 1) * d.W;
   d.meas_bpl = std::max<uint32_t>(1, (d.Ly * d.W + kMeasureItemsPerBlock - 1) / kMeasureItemsPerBlock);
+  d.meas_lpu = 1;
+  if (2 * d.Ly * d.W <= kMeasureItemsPerBlock)
+    d.meas_lpu = std::min<uint32_t>({kMeasureMaxLpu, d.Lx, kMeasureItemsPerBlock / (d.Ly * d.W)});
   d.active = 1;
   d.sweep_end = 0xFFFFFFFFu;
   fastdiv_magic(d.W, &d.divw_m, &d.divw_l);
@@ -138,7 +141,7 @@ void FilmSet::layout(bool assign_part) {
     d.meas_block_begin = mb;
     if (assign_part) d.part_off = po;
     ub += (d.upd_items + items_per_block(items) - 1) / items_per_block(items);
-    mb += d.Lx * d.meas_bpl;
+    mb += meas_units(d);
     po += part_len(d);
   }
   hh.n_films = (uint32_t)h.size();
@@ -169,7 +172,7 @@ int FilmSet::upload() {
     const FilmDesc& d = h[f];
     const uint32_t nb = (d.upd_items + items_per_block(items) - 1) / items_per_block(items);
     for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
-    for (uint32_t b = 0; b < d.Lx * d.meas_bpl; b++) om[d.meas_block_begin + b] = (uint32_t)f;
+    for (uint32_t b = 0; b < meas_units(d); b++) om[d.meas_block_begin + b] = (uint32_t)f;
   }
   L.hdr = reinterpret_cast<LaunchHdr*>(d_meta);
   L.films = reinterpret_cast<FilmDesc*>(d_meta + sizeof hh);
@@ -489,6 +492,12 @@ int ising_set_sweep(ising* h, uint64_t sweep) {
   h->d().sweep = (uint32_t)sweep;
   h->dirty = true;
   return sync_desc(h);
+}
+
+int ising_reserve_records(ising* h, uint64_t n_records) {
+  clear_error();
+  if (!h) return fail(ISING_EINVAL, "NULL handle");
+  return ensure_ring(h, n_records);
 }
 
 int ising_set_shape(ising* h, int shape) {

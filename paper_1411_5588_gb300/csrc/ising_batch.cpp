@@ -264,6 +264,14 @@ int ising_batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
   return ISING_OK;
 }
 
+int ising_batch_reserve_records(ising_batch* b, uint64_t n_records) {
+  clear_error();
+  if (!b) return fail(ISING_EINVAL, "NULL batch");
+  std::vector<uint64_t> extra(b->fs.h.size());
+  for (size_t f = 0; f < extra.size(); f++) extra[f] = b->fs.h[f].measure_every ? n_records : 0;
+  return batch_ensure_rings(b, extra);
+}
+
 int ising_batch_set_shape(ising_batch* b, int shape) {
   clear_error();
   if (!b) return fail(ISING_EINVAL, "NULL batch");

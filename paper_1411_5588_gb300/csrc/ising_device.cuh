@@ -56,7 +56,7 @@ struct FilmDesc {
   uint32_t thr[4][16];         // Metropolis thresholds [class][s + 2*n_aligned]
   uint32_t always[4];          // bit (s + 2*n_aligned): accept without a draw
   uint32_t has_never;          // some reachable entry has dE > 0 and thr = 0
-  uint32_t reserved;
+  uint32_t meas_lpu;           // layers per measurement block (> 1 only when meas_bpl = 1)
   uint32_t rk0[10], rk1[10];   // Philox round keys: key + r * Weyl constant
   uint32_t reserved2[4];
 };

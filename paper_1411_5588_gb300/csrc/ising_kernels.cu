@@ -395,6 +395,7 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
                        const LaunchHdr* __restrict__ hdr, const uint32_t* __restrict__ pool,
                        int64_t* __restrict__ part, uint32_t done, int force) {
   __shared__ int64_t s_red[kMeasureBlock / 32];
+  __shared__ int s_m[kMeasureMaxLpu];
   pdl_trigger();
   pdl_wait();
   const uint32_t nvb = hdr->meas_blocks;
@@ -402,6 +403,49 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
     const FilmDesc& F = films[owner[vb]];
     if (!F.active || !measured_now(F, done, force)) continue;
     const uint32_t Lx = F.Lx, Ly = F.Ly, W = F.W, bpl = F.meas_bpl;
+    if (F.meas_lpu > 1) {
+      // several small layers per block: layer sums by shared atomics, one
+      // bond-sum reduction; the bond sum goes to the first layer's slot
+      const uint32_t* A = pool + F.spin_off;
+      const uint32_t* B = A + (size_t)Lx * Ly * F.Wp;
+      const uint32_t kx0 = (vb - F.meas_block_begin) * F.meas_lpu;
+      const uint32_t nl = min(F.meas_lpu, Lx - kx0);
+      const uint32_t per = Ly * W, total = nl * per;
+      for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) s_m[i] = 0;
+      __syncthreads();
+      int64_t bsum = 0;
+      for (uint32_t base = 0; base < total; base += blockDim.x) {
+        const uint32_t it = base + threadIdx.x;
+        const bool on = it < total;
+        int m = 0, bb = 0;
+        uint32_t l = 0xFFFFFFFFu;
+        if (on) {
+          l = it / per;
+          const uint32_t r = it - l * per, kym1 = r / W;
+          measure_word(A, B, F.Wp, Lx, Ly, W, F.n, F.last_mask, F.x_pbc, F.y_mode, kx0 + l, kym1, r - kym1 * W, m,
+                       bb);
+          bsum += bb;
+        }
+        const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, l, 0);
+        if (__all_sync(0xFFFFFFFFu, !on || l == l0)) {
+          int v = m;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+          if ((threadIdx.x & 31u) == 0 && l0 != 0xFFFFFFFFu) atomicAdd(&s_m[l0], v);
+        } else if (on) {
+          atomicAdd(&s_m[l], m);
+        }
+      }
+      const int64_t tb = block_sum(bsum, s_red);  // its barriers also complete s_m
+      for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) {
+        int64_t* p = part + F.part_off + 2 * (size_t)(kx0 + i);
+        p[0] = s_m[i];
+        if (i != 0) p[1] = 0;
+      }
+      if (threadIdx.x == 0) part[F.part_off + 2 * (size_t)kx0 + 1] = tb;
+      __syncthreads();  // s_m is read above before the next block clears it
+      continue;
+    }
     const uint32_t local = vb - F.meas_block_begin;
     const uint32_t kxm1 = local / bpl, chunk = local % bpl;
     const uint32_t Wp = F.Wp;

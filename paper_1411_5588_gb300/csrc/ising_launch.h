@@ -21,8 +21,16 @@ constexpr int kMultiMinBlocks = 6;
 inline uint32_t items_per_block(uint32_t items) { return kFilmThreads * items; }
 constexpr int kMeasureBlock = 256;
 
-// Items a measurement block covers per layer before another block is added.
+// Items a measurement block covers per layer before another block is added;
+// layers of fewer than kMeasureItemsPerBlock / 2 words are grouped, up to
+// kMeasureMaxLpu of them per block.
 constexpr uint32_t kMeasureItemsPerBlock = 4 * kMeasureBlock;
+constexpr uint32_t kMeasureMaxLpu = 64;
+
+// Measurement blocks of one film.
+inline uint32_t meas_units(const FilmDesc& d) {
+  return d.meas_lpu > 1 ? (d.Lx + d.meas_lpu - 1) / d.meas_lpu : d.Lx * d.meas_bpl;
+}
 
 // Resident path: one block per film holds the film's packed planes in shared
 // memory (row stride W) for a whole run of sweeps, records included.  Films

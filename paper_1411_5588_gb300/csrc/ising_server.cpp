@@ -313,7 +313,7 @@ void ising_server::loop() {
         const FilmDesc& d = fs.h[f];
         const uint32_t nb = (d.upd_items + items_per_block(fs.items) - 1) / items_per_block(fs.items);
         for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
-        for (uint32_t b = 0; b < d.Lx * d.meas_bpl; b++) om[d.meas_block_begin + b] = (uint32_t)f;
+        for (uint32_t b = 0; b < meas_units(d); b++) om[d.meas_block_begin + b] = (uint32_t)f;
       }
       // pinned space for the results of the jobs finishing in this chunk
       size_t need = 0;
