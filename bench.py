@@ -32,6 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 SHAPE_NAMES = {0: "auto", 1: "resident", 2: "grid, 1 word/thread", 3: "grid, 2 words/thread"}
+SHAPE_FLAGS = {1: "resident", 2: "grid1", 3: "grid2"}
 METRIC = "spin-flip attempts/ns on 1 GB300, batched vs plain, % roofline; p99 latency"
 UNIT = "attempts/ns"
 SWEEPS_PER_STEP = 10
@@ -55,16 +56,17 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def profiled_traffic():
+def profiled_traffic(shape):
     """dram bytes per update launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+    taken on the current kernel source in the launch shape this run used."""
     try:
         text = open(PROFILE).read()
     except OSError:
         return None
     m = re.search(r"kernel-source-sha1:\s*([0-9a-f]{40})", text)
     t = re.search(r"dram-bytes-per-launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    s = re.search(r"launch-shape:\s*(\S+)", text)
+    if not m or not t or not s or m.group(1) != kernel_source_hash() or s.group(1) != SHAPE_FLAGS[shape]:
         return None
     return float(t.group(1))
 
@@ -394,6 +396,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/serving/e2e/cpu legs")
     ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--shape", default="auto", choices=["auto", "grid1", "grid2"],
+                    help="launch shape of the 120x240x1600 film (auto: the library's autotuner); profiling "
+                         "pins the autotuner's normal pick because ncu's serialisation distorts its timing")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -418,8 +423,12 @@ def main():
     film.init(job["init_kind"], job["flip_p"])
     # launch shapes picked by the library's autotuner (on a scratch film),
     # for the timed steps and for the update-kernel timing pass below
-    shape_step = SHAPE_NAMES[film.autotune(SWEEPS_PER_STEP)]
-    shape_kernel = SHAPE_NAMES[film.autotune(0)]
+    if args.shape == "auto":
+        code_step, code_kernel = film.autotune(SWEEPS_PER_STEP), film.autotune(0)
+    else:
+        code_step = code_kernel = {"grid1": ig.SHAPE_GRID_1, "grid2": ig.SHAPE_GRID_2}[args.shape]
+        film.set_shape(code_step)
+    shape_step, shape_kernel = SHAPE_NAMES[code_step], SHAPE_NAMES[code_kernel]
     sites = WL.sites(job)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -437,12 +446,14 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_timed")  # ncu --nvtx-include bench_timed/ profiles these steps only
         for e0, e1 in events:
             flush.fill_(1)  # evict L2 (inputs smaller than L2)
             e0.record(stream)
             film.sweep(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
             e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         if world > 1:
             torch.distributed.barrier()
         clocks = sampler.stop()
@@ -466,7 +477,7 @@ def main():
     achieved = ops_per_launch / (upd_ms * 1e-3) / 1e12
     peak = N_SM * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(), "kernel": "update_film_kernel",
+                "traffic": profiled_traffic(code_kernel), "kernel": "update_film_kernel",
                 "launch_us": upd_ms * 1e3, "ops_per_attempt": OPS_PER_ATTEMPT,
                 "peak_from": "152 SMs x 128 int32 lanes x 2.07 GHz (nominal max clock)",
                 "attempts_per_ns_at_peak": peak * 1e3 / OPS_PER_ATTEMPT}

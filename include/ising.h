@@ -149,7 +149,9 @@ int ising_get_shape(ising *h, uint32_t measure_every, int *shape);
  * every measure_every sweeps, so this handle's chain is not touched.  The
  * fastest goes into a process-wide table keyed by (Lx, Ly, Lz, boundary
  * modes, table variant, record interval up to 16) that every AUTO handle of
- * that key then uses; *shape (may be NULL) receives it.  Synchronises. */
+ * that key then uses; *shape (may be NULL) receives it.  Shapes are tried
+ * in the order RESIDENT, GRID_1, GRID_2, and a later one must be at least 2%
+ * faster to win.  Synchronises. */
 int ising_autotune(ising *h, uint32_t measure_every, int *shape);
 
 /* Enqueue n_sweeps sweeps on the handle's stream (asynchronous).  After every

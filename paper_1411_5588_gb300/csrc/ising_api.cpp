@@ -552,7 +552,7 @@ int ising_autotune(ising* h, uint32_t measure_every, int* shape) {
       size_t got = 0;
       if (!rc) rc = ising_read_series(s, drain.data(), (size_t)(s->rec_written - s->rec_read), &got);
     }
-    if (!rc && ms < best_ms) {
+    if (!rc && ms < kTuneMargin * best_ms) {  // a later shape must win clearly
       best_ms = ms;
       best = cand;
     }

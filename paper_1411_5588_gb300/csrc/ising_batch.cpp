@@ -320,7 +320,7 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
       if (!rc && rep > 0) ms = std::min(ms, t);
       for (size_t f = 0; f < s->fs.h.size(); f++) s->rec_read[f] = s->rec_written[f];  // drop the records
     }
-    if (!rc && ms < best_ms) {
+    if (!rc && ms < kTuneMargin * best_ms) {  // two words per thread must win clearly
       best_ms = ms;
       best = items;
     }

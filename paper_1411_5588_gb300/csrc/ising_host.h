@@ -79,6 +79,12 @@ struct FilmSet {
   ~FilmSet() { release(); }
 };
 
+// A candidate launch shape replaces the autotuner's current best only when it
+// is this much faster (candidates are tried in the order RESIDENT, GRID_1,
+// GRID_2), so that shapes within timing noise of each other resolve the same
+// way on every run.
+constexpr float kTuneMargin = 0.98f;
+
 // Autotuner cache, shared by every handle of the process: the fastest launch
 // shape (ISING_SHAPE_*) measured for a film shape, boundary, table variant
 // and record interval.
