@@ -31,8 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-SHAPE_NAMES = {0: "auto", 1: "resident", 2: "grid, 1 word/thread", 3: "grid, 2 words/thread"}
-SHAPE_FLAGS = {1: "resident", 2: "grid1", 3: "grid2"}
+SHAPE_NAMES = {0: "auto", 1: "resident", 2: "grid, 1 word/thread", 3: "grid, 2 words/thread",
+               4: "grid, 4 threads/word"}
+SHAPE_FLAGS = {1: "resident", 2: "grid1", 3: "grid2", 4: "gridq"}
 METRIC = "spin-flip attempts/ns on 1 GB300, batched vs plain, % roofline; p99 latency"
 UNIT = "attempts/ns"
 SWEEPS_PER_STEP = 10

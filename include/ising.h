@@ -75,11 +75,15 @@ enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
  * GRID_1    two grid launches per sweep (plus the record kernels), one
  *           32-site word per thread: the shortest launch latency;
  * GRID_2    the same with two words per thread, which overlaps one word's
- *           loads with the other's arithmetic.
+ *           loads with the other's arithmetic;
+ * GRID_Q    the same with four threads per word, each drawing two of its
+ *           eight Philox calls: four times the threads for the same work,
+ *           for films too small to fill the GPU otherwise.
  * AUTO      the autotuner's measurement for this film shape and record
  *           interval if there is one, else RESIDENT up to 32768 spins and
  *           GRID_1 above. */
-enum { ISING_SHAPE_AUTO = 0, ISING_SHAPE_RESIDENT = 1, ISING_SHAPE_GRID_1 = 2, ISING_SHAPE_GRID_2 = 3 };
+enum { ISING_SHAPE_AUTO = 0, ISING_SHAPE_RESIDENT = 1, ISING_SHAPE_GRID_1 = 2, ISING_SHAPE_GRID_2 = 3,
+       ISING_SHAPE_GRID_Q = 4 };
 
 typedef struct ising ising;
 
@@ -150,7 +154,7 @@ int ising_get_shape(ising *h, uint32_t measure_every, int *shape);
  * fastest goes into a process-wide table keyed by (Lx, Ly, Lz, boundary
  * modes, table variant, record interval up to 16) that every AUTO handle of
  * that key then uses; *shape (may be NULL) receives it.  Shapes are tried
- * in the order RESIDENT, GRID_1, GRID_2, and a later one must be at least 2%
+ * in the order RESIDENT, GRID_1, GRID_2, GRID_Q, and a later one must be at least 2%
  * faster to win.  Synchronises. */
 int ising_autotune(ising *h, uint32_t measure_every, int *shape);
 
@@ -216,13 +220,13 @@ int ising_batch_sweep(ising_batch *b, uint64_t n_sweeps, int use_graph);
  * ising_reserve_records).  ENOMEM. */
 int ising_batch_reserve_records(ising_batch *b, uint64_t n_records);
 
-/* Launch shape of the batch's grid kernels: GRID_1, GRID_2, or AUTO (the
+/* Launch shape of the batch's grid kernels: GRID_1, GRID_2, GRID_Q, or AUTO (the
  * autotuner's choice once ising_batch_autotune has run, else GRID_1).
  * RESIDENT is EINVAL for a batch.  Changing it drops the captured graphs. */
 int ising_batch_set_shape(ising_batch *b, int shape);
 int ising_batch_get_shape(ising_batch *b, int *shape);
 
-/* Autotuner: times GRID_1 and GRID_2 on a scratch batch of the same jobs
+/* Autotuner: times GRID_1, GRID_2 and GRID_Q on a scratch batch of the same jobs
  * (from their initial states; the kernels' work does not depend on the
  * spins), graph replay and records included, and adopts the faster unless
  * a shape is pinned; *shape (may be NULL) receives it.  Synchronises. */

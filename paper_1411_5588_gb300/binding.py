@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = range(7)
 Y_GAPBC, Y_PBC, Y_APBC = 0, 1, 2
 X_FREE, X_PBC = 0, 1
 INIT_RANDOM, INIT_SLAB_Y, INIT_ALL_UP = 0, 1, 2
-SHAPE_AUTO, SHAPE_RESIDENT, SHAPE_GRID_1, SHAPE_GRID_2 = 0, 1, 2, 3
+SHAPE_AUTO, SHAPE_RESIDENT, SHAPE_GRID_1, SHAPE_GRID_2, SHAPE_GRID_Q = 0, 1, 2, 3, 4
 
 _c = ctypes
 P = _c.c_void_p

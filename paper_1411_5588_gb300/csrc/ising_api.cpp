@@ -140,7 +140,7 @@ void FilmSet::layout(bool assign_part) {
     d.upd_block_begin = ub;
     d.meas_block_begin = mb;
     if (assign_part) d.part_off = po;
-    ub += (d.upd_items + items_per_block(items) - 1) / items_per_block(items);
+    ub += (d.upd_items + words_per_block(items) - 1) / words_per_block(items);
     mb += meas_units(d);
     po += part_len(d);
   }
@@ -170,7 +170,7 @@ int FilmSet::upload() {
   uint32_t* om = ou + hh.upd_blocks;
   for (size_t f = 0; f < nf; f++) {
     const FilmDesc& d = h[f];
-    const uint32_t nb = (d.upd_items + items_per_block(items) - 1) / items_per_block(items);
+    const uint32_t nb = (d.upd_items + words_per_block(items) - 1) / words_per_block(items);
     for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
     for (uint32_t b = 0; b < meas_units(d); b++) om[d.meas_block_begin + b] = (uint32_t)f;
   }
@@ -503,7 +503,7 @@ int ising_reserve_records(ising* h, uint64_t n_records) {
 int ising_set_shape(ising* h, int shape) {
   clear_error();
   if (!h) return fail(ISING_EINVAL, "NULL handle");
-  if (shape < ISING_SHAPE_AUTO || shape > ISING_SHAPE_GRID_2) return fail(ISING_EINVAL, "unknown shape %d", shape);
+  if (shape < ISING_SHAPE_AUTO || shape > ISING_SHAPE_GRID_Q) return fail(ISING_EINVAL, "unknown shape %d", shape);
   if (shape == ISING_SHAPE_RESIDENT && !resident_smem_bytes(h->d()))
     return fail(ISING_EINVAL, "film too large for the resident kernel");
   h->shape = shape;
@@ -536,7 +536,7 @@ int ising_autotune(ising* h, uint32_t measure_every, int* shape) {
   int best = ISING_SHAPE_GRID_1;
   float best_ms = 3.0e38f;
   std::vector<int64_t> drain;
-  for (int cand = ISING_SHAPE_RESIDENT; !rc && cand <= ISING_SHAPE_GRID_2; cand++) {
+  for (int cand = ISING_SHAPE_RESIDENT; !rc && cand <= ISING_SHAPE_GRID_Q; cand++) {
     if (cand == ISING_SHAPE_RESIDENT && !resident_smem_bytes(d)) continue;
     s->shape = cand;
     float ms = 3.0e38f;
@@ -594,7 +594,7 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
     return ISING_OK;
   }
   // single film: the descriptor travels as a kernel parameter
-  const uint32_t items = shape == ISING_SHAPE_GRID_2 ? 2u : 1u;
+  const uint32_t items = shape_items(shape);
   for (uint64_t k = 0; k < n; k++) {
     const uint32_t t = (uint32_t)(s0 + k);
     ISG_CK(launch_update_film(d, h->fs.pool, 0, t, items, h->fs.stream));

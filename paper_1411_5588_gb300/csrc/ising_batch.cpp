@@ -25,7 +25,7 @@ struct ising_batch {
   size_t stage_bytes = 0;
   bool dirty = true;
   int shape = ISING_SHAPE_AUTO;  // pinned launch shape, or AUTO
-  uint32_t tuned_items = 0;      // ising_batch_autotune's choice (0: none yet)
+  int tuned_shape = 0;           // ising_batch_autotune's choice (0: none yet)
   std::map<uint32_t, cudaGraphExec_t> graphs;  // chunk length -> executable graph
 
   void drop_graphs() {
@@ -275,19 +275,19 @@ int ising_batch_reserve_records(ising_batch* b, uint64_t n_records) {
 int ising_batch_set_shape(ising_batch* b, int shape) {
   clear_error();
   if (!b) return fail(ISING_EINVAL, "NULL batch");
-  if (shape != ISING_SHAPE_AUTO && shape != ISING_SHAPE_GRID_1 && shape != ISING_SHAPE_GRID_2)
-    return fail(ISING_EINVAL, "batches take AUTO, GRID_1 or GRID_2");
+  if (shape != ISING_SHAPE_AUTO && shape != ISING_SHAPE_GRID_1 && shape != ISING_SHAPE_GRID_2 &&
+      shape != ISING_SHAPE_GRID_Q)
+    return fail(ISING_EINVAL, "batches take AUTO, GRID_1, GRID_2 or GRID_Q");
   b->shape = shape;
-  const uint32_t items = shape == ISING_SHAPE_GRID_2 ? 2u
-                         : shape == ISING_SHAPE_GRID_1 ? 1u
-                                                       : (b->tuned_items ? b->tuned_items : 1u);
+  const uint32_t items = shape == ISING_SHAPE_AUTO ? (b->tuned_shape ? shape_items(b->tuned_shape) : 1u)
+                                                   : shape_items(shape);
   return apply_items(b, items);
 }
 
 int ising_batch_get_shape(ising_batch* b, int* shape) {
   clear_error();
   if (!b || !shape) return fail(ISING_EINVAL, "NULL argument");
-  *shape = b->fs.items == 2 ? ISING_SHAPE_GRID_2 : ISING_SHAPE_GRID_1;
+  *shape = items_shape(b->fs.items);
   return ISING_OK;
 }
 
@@ -305,10 +305,10 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(ISING_ECUDA, "event creation failed");
-  uint32_t best = 1;
+  int best = ISING_SHAPE_GRID_1;
   float best_ms = 3.0e38f;
-  for (uint32_t items = 1; !rc && items <= kMaxFilmItems; items++) {
-    rc = apply_items(s, items);
+  for (int cand = ISING_SHAPE_GRID_1; !rc && cand <= ISING_SHAPE_GRID_Q; cand++) {
+    rc = apply_items(s, shape_items(cand));
     float ms = 3.0e38f;
     for (int rep = 0; !rc && rep < 3; rep++) {  // the first run captures the graph
       if (cudaEventRecord(e0, s->fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
@@ -320,18 +320,18 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
       if (!rc && rep > 0) ms = std::min(ms, t);
       for (size_t f = 0; f < s->fs.h.size(); f++) s->rec_read[f] = s->rec_written[f];  // drop the records
     }
-    if (!rc && ms < kTuneMargin * best_ms) {  // two words per thread must win clearly
+    if (!rc && ms < kTuneMargin * best_ms) {  // a later shape must win clearly
       best_ms = ms;
-      best = items;
+      best = cand;
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   ising_batch_destroy(s);
   if (rc) return rc;
-  b->tuned_items = best;
-  if (b->shape == ISING_SHAPE_AUTO) rc = apply_items(b, best);
-  if (!rc && shape) *shape = best == 2 ? ISING_SHAPE_GRID_2 : ISING_SHAPE_GRID_1;
+  b->tuned_shape = best;
+  if (b->shape == ISING_SHAPE_AUTO) rc = apply_items(b, shape_items(best));
+  if (!rc && shape) *shape = best;
   return rc;
 }
 

@@ -47,7 +47,7 @@ struct FilmSet {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int n_sm = 0, upd_per_sm = 0, meas_per_sm = 0;
-  uint32_t items = 1;  // words per thread of the grid update kernel (1 or 2)
+  uint32_t items = 1;  // words per thread of the grid update kernel (1, 2; 0 = four threads per word)
 
   std::vector<FilmDesc> h;  // host mirror (counters tracked on the host too)
   LaunchHdr hh{};
@@ -81,9 +81,17 @@ struct FilmSet {
 
 // A candidate launch shape replaces the autotuner's current best only when it
 // is this much faster (candidates are tried in the order RESIDENT, GRID_1,
-// GRID_2), so that shapes within timing noise of each other resolve the same
-// way on every run.
+// GRID_2, GRID_Q), so that shapes within timing noise of each other resolve
+// the same way on every run.
 constexpr float kTuneMargin = 0.98f;
+
+// Grid kernel words-per-thread code of a grid shape, and back.
+inline uint32_t shape_items(int shape) {
+  return shape == ISING_SHAPE_GRID_2 ? 2u : shape == ISING_SHAPE_GRID_Q ? 0u : 1u;
+}
+inline int items_shape(uint32_t items) {
+  return items == 2 ? ISING_SHAPE_GRID_2 : items == 0 ? ISING_SHAPE_GRID_Q : ISING_SHAPE_GRID_1;
+}
 
 // Autotuner cache, shared by every handle of the process: the fastest launch
 // shape (ISING_SHAPE_*) measured for a film shape, boundary, table variant

@@ -84,11 +84,13 @@ __device__ __forceinline__ void fetch_word(const FilmCtx& c, uint32_t kx, uint32
 }
 
 // Metropolis decisions for the up to 32 sites of the fetched word; returns
-// the new word.
-template <bool FULL, bool FAST>
+// the mask of sites that flip.  QUARTER: only Philox calls qsel and qsel + 4
+// (the sites at bits qsel and qsel + 4 of each byte), for a word shared by
+// four lanes.
+template <bool FULL, bool FAST, bool QUARTER>
 __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched& f,
                                                 const uint32_t* __restrict__ s_thr,
-                                                const uint32_t* __restrict__ s_alw) {
+                                                const uint32_t* __restrict__ s_alw, uint32_t qsel) {
   const uint32_t Lx = c.Lx, Ly = c.Ly, W = c.W;
   const uint32_t kx = f.kx, ky = f.ky, w = f.w;
   const uint32_t row = (kx - 1) * Ly + (ky - 1);
@@ -161,14 +163,13 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const PhiloxRow pr(row, c.sweep, X, c.rk0, c.rk1);
   uint32_t lt = 0;
   // calls q and q + 4 are drawn together (two independent Philox chains)
-#pragma unroll
-  for (uint32_t q = 0; q < 4; q++) {
+  auto calls = [&](uint32_t q, uint32_t Uq) {
     if (FULL || q < ncalls) {
       uint32_t u[4], v[4];
       pr.draw2(8u * w + q, 8u * w + q + 4, u, v);
       const bool two = FULL || q + 4 < ncalls;
-      const uint32_t Y = ((U[q] << 2) & 0x3C3C3C3Cu) | clsb;
-      const uint32_t Y2 = ((U[q] >> 2) & 0x3C3C3C3Cu) | clsb;
+      const uint32_t Y = ((Uq << 2) & 0x3C3C3C3Cu) | clsb;
+      const uint32_t Y2 = ((Uq >> 2) & 0x3C3C3C3Cu) | clsb;
 #pragma unroll
       for (uint32_t i = 0; i < 4; i++) {
         if (FAST) {
@@ -186,9 +187,16 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
         }
       }
     }
+  };
+  if (QUARTER) {
+    const uint32_t Uq = qsel == 0 ? U[0] : qsel == 1 ? U[1] : qsel == 2 ? U[2] : U[3];
+    calls(qsel, Uq);
+  } else {
+#pragma unroll
+    for (uint32_t q = 0; q < 4; q++) calls(q, U[q]);
   }
   const uint32_t valid = FULL ? 0xFFFFFFFFu : c.last_mask;
-  return S ^ ((lt | alw) & valid);
+  return (lt | alw) & valid;
 }
 
 __device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, uint32_t v) {
@@ -211,7 +219,8 @@ template <bool FAST>
 __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
                                                const uint32_t* s_alw) {
   const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
-  const uint32_t v = full ? decide_word<true, FAST>(c, f, s_thr, s_alw) : decide_word<false, FAST>(c, f, s_thr, s_alw);
+  const uint32_t v = f.S ^ (full ? decide_word<true, FAST, false>(c, f, s_thr, s_alw, 0)
+                                 : decide_word<false, FAST, false>(c, f, s_thr, s_alw, 0));
   store_word(c, f, v);
   // ky = 1 rows then update their wrap partner row (kx', Ly); its wrap
   // neighbour is the word just written, so it is fetched only now
@@ -219,23 +228,68 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
     const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
     Fetched g;
     fetch_word(c, kx2, c.Ly, f.w, g);
-    const uint32_t v2 = full ? decide_word<true, FAST>(c, g, s_thr, s_alw) : decide_word<false, FAST>(c, g, s_thr, s_alw);
+    const uint32_t v2 = g.S ^ (full ? decide_word<true, FAST, false>(c, g, s_thr, s_alw, 0)
+                                    : decide_word<false, FAST, false>(c, g, s_thr, s_alw, 0));
     store_word(c, g, v2);
   }
 }
 
+// The same for a word shared by the four lanes 4j..4j+3 of a warp (lane qsel
+// draws Philox calls qsel and qsel + 4); gmask holds the lanes whose group has
+// a word.  The lanes merge their flip masks and the group's lane 0 stores.
+template <bool FAST>
+__device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const Fetched& f, bool on, uint32_t qsel,
+                                                       uint32_t gmask, const uint32_t* s_thr,
+                                                       const uint32_t* s_alw) {
+  const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
+  uint32_t fl = 0;
+  if (on) fl = full ? decide_word<true, FAST, true>(c, f, s_thr, s_alw, qsel)
+                    : decide_word<false, FAST, true>(c, f, s_thr, s_alw, qsel);
+  if (!on) return;
+  fl |= __shfl_xor_sync(gmask, fl, 1);
+  fl |= __shfl_xor_sync(gmask, fl, 2);
+  if (qsel == 0) store_word(c, f, f.S ^ fl);
+  // ky = 1 words then update their wrap partner word (see update_fetched)
+  const uint32_t pmask = __ballot_sync(gmask, f.ky == 1);
+  if (f.ky != 1) return;
+  __syncwarp(pmask);  // the partner's wrap neighbour is the word stored above
+  const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
+  Fetched g;
+  fetch_word(c, kx2, c.Ly, f.w, g);
+  uint32_t fl2 = full ? decide_word<true, FAST, true>(c, g, s_thr, s_alw, qsel)
+                      : decide_word<false, FAST, true>(c, g, s_thr, s_alw, qsel);
+  fl2 |= __shfl_xor_sync(pmask, fl2, 1);
+  fl2 |= __shfl_xor_sync(pmask, fl2, 2);
+  if (qsel == 0) store_word(c, g, g.S ^ fl2);
+}
+
 }  // namespace
 
-// The words of one block of ITEMS * kFilmThreads consecutive words: each
-// thread fetches its ITEMS words (kFilmThreads apart) before deciding any.
+// The words of one block of words_per_block(ITEMS) consecutive words: each
+// thread fetches its ITEMS words (kFilmThreads apart) before deciding any;
+// ITEMS = 0: four lanes per word (kFilmThreads / 4 words).
 template <bool FAST, uint32_t ITEMS>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw) {
-  Fetched fw[ITEMS];
-  bool mine[ITEMS];
+  if (ITEMS == 0) {
+    const uint32_t item = first + (threadIdx.x >> 2);
+    const bool on = item < items;
+    const uint32_t gmask = __ballot_sync(0xFFFFFFFFu, on);
+    Fetched f;
+    if (on) {
+      uint32_t kx, ky, w;
+      item_word(c, item, dwm, dwl, dym, dyl, kx, ky, w);
+      fetch_word(c, kx, ky, w, f);
+    }
+    update_fetched_quarter<FAST>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw);
+    return;
+  }
+  constexpr uint32_t NI = ITEMS == 0 ? 1 : ITEMS;
+  Fetched fw[NI];
+  bool mine[NI];
 #pragma unroll
-  for (uint32_t it = 0; it < ITEMS; it++) {
+  for (uint32_t it = 0; it < NI; it++) {
     const uint32_t item = first + threadIdx.x + it * kFilmThreads;
     mine[it] = item < items;
     if (mine[it]) {
@@ -245,11 +299,11 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
     }
   }
 #pragma unroll
-  for (uint32_t it = 0; it < ITEMS; it++)
+  for (uint32_t it = 0; it < NI; it++)
     if (mine[it]) update_fetched<FAST>(c, fw[it], s_thr, s_alw);
 }
 
-// Half-sweep of every film of a launch: block b handles ITEMS * kFilmThreads
+// Half-sweep of every film of a launch: block b handles words_per_block(ITEMS)
 // words of film owner[b], whose descriptor is staged in shared memory.  FAST:
 // no film of the launch has a reachable thr = 0 entry (the compare-only
 // table); otherwise every film takes the exact variant.
@@ -286,14 +340,14 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     c.colour = colour; c.sweep = s_d.sweep + k;
     c.plane0 = pool + s_d.spin_off;
     c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
-    const uint32_t first = (vb - s_d.upd_block_begin) * (ITEMS * kFilmThreads);
+    const uint32_t first = (vb - s_d.upd_block_begin) * words_per_block(ITEMS);
     sweep_block<FAST, ITEMS>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
   }
 }
 
 // Single-film half-sweep.  The descriptor is a __grid_constant__ kernel
 // parameter, so every per-film constant (round keys included) is read straight
-// from the constant bank; block b updates words b * ITEMS * kFilmThreads
+// from the constant bank; block b updates words b * words_per_block(ITEMS)
 // onwards.
 template <bool FAST, uint32_t ITEMS>
 __global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
@@ -316,7 +370,7 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   c.colour = colour; c.sweep = sweep;
   c.plane0 = pool + d.spin_off;
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
-  sweep_block<FAST, ITEMS>(c, blockIdx.x * (ITEMS * kFilmThreads), d.upd_items, d.divw_m, d.divw_l, d.divy_m, d.divy_l, s_thr,
+  sweep_block<FAST, ITEMS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m, d.divy_l, s_thr,
                     s_alw);
 }
 
@@ -739,19 +793,22 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, 
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
                           uint32_t items, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  auto* kern = exact ? (items == 2 ? update_kernel<false, 2> : update_kernel<false, 1>)
-                     : (items == 2 ? update_kernel<true, 2> : update_kernel<true, 1>);
+  auto* kern = exact ? (items == 2 ? update_kernel<false, 2> : items == 1 ? update_kernel<false, 1> : update_kernel<false, 0>)
+                     : (items == 2 ? update_kernel<true, 2> : items == 1 ? update_kernel<true, 1> : update_kernel<true, 0>);
   return launch_pdl(kern, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
                     (const LaunchHdr*)L.hdr, pool, colour, k);
 }
 
 cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep, uint32_t items,
                                cudaStream_t st) {
-  const uint32_t ipb = items_per_block(items);
+  const uint32_t ipb = words_per_block(items);
   const uint32_t grid = (d.upd_items + ipb - 1) / ipb;
   if (grid == 0) return cudaSuccess;
-  auto* kern = d.has_never ? (items == 2 ? update_film_kernel<false, 2> : update_film_kernel<false, 1>)
-                           : (items == 2 ? update_film_kernel<true, 2> : update_film_kernel<true, 1>);
+  auto* kern = d.has_never
+                   ? (items == 2 ? update_film_kernel<false, 2> : items == 1 ? update_film_kernel<false, 1>
+                                                                             : update_film_kernel<false, 0>)
+                   : (items == 2 ? update_film_kernel<true, 2> : items == 1 ? update_film_kernel<true, 1>
+                                                                            : update_film_kernel<true, 0>);
   return launch_pdl(kern, grid, kFilmThreads, 0, st, d, pool, colour, sweep);
 }
 

@@ -15,10 +15,13 @@ namespace isg {
 // (small and medium films are latency bound), two let each thread overlap
 // the loads of its second word with the first word's arithmetic.
 constexpr uint32_t kFilmThreads = 128;
-constexpr uint32_t kMaxFilmItems = 2;
 constexpr int kFilmMinBlocks = 6;
 constexpr int kMultiMinBlocks = 6;
-inline uint32_t items_per_block(uint32_t items) { return kFilmThreads * items; }
+// items = 0 is the quarter shape: four lanes share each word (they split its
+// eight Philox calls), so a block covers kFilmThreads / 4 words.
+__host__ __device__ constexpr uint32_t words_per_block(uint32_t items) {
+  return items == 0 ? kFilmThreads / 4 : kFilmThreads * items;
+}
 constexpr int kMeasureBlock = 256;
 
 // Items a measurement block covers per layer before another block is added;
@@ -53,7 +56,8 @@ struct LaunchSet {
 };
 
 // exact: some film of the launch has a reachable thr = 0 entry (has_never);
-// items: words per thread (1 or 2), matching the owner table's block size.
+// items: words per thread (1 or 2, or 0 for four lanes per word), matching the
+// owner table's block size.
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
                           uint32_t items, cudaStream_t st);
 // One half-sweep of a single film whose descriptor (with `sweep` absolute) is

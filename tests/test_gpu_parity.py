@@ -47,14 +47,15 @@ def _pair(case, seed=7, replica=3, shape=ig.SHAPE_AUTO):
     return g, o
 
 
-SHAPES = [ig.SHAPE_RESIDENT, ig.SHAPE_GRID_1, ig.SHAPE_GRID_2]
+SHAPES = [ig.SHAPE_RESIDENT, ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2"])
+@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2", "gridq"])
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-y{c[3]}x{c[4]}-T{c[7]}" for c in CASES])
 def test_sweeps_bit_exact(case, shape):
     """Every launch shape: the resident kernel (the film in shared memory for
-    the whole call) and the grid kernels with one or two words per thread."""
+    the whole call) and the grid kernels with one or two words per thread or
+    four threads per word."""
     g, o = _pair(case, shape=shape)
     assert np.array_equal(g.get_spins(), o.get_spins()), "initial state differs"
     done = 0
@@ -135,18 +136,20 @@ def test_paper_scale_film_bit_exact():
     +H1 = 0.55 at T = 3, in the launch configuration the benchmark times
     (records every 10 sweeps)."""
     Lx, Ly, Lz = 120, 240, 1600
-    g = ig.Film(Lx, Ly, Lz, 1.0, 0.55, 3.0, 2)
     o = O.Film(Lx, Ly, Lz, 1.0, 0.55, 3.0, 2)
-    g.init(ig.INIT_SLAB_Y, 0.01)
     o.init(O.INIT_SLAB_Y, 0.01)
-    g.sweep(20, 10)
     want = o.sweep(20, 10)
-    assert np.array_equal(g.read_series(), want)
-    assert np.array_equal(g.get_spins(), o.get_spins())
-    g.close()
+    spins = o.get_spins()
+    for shape in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q):
+        g = ig.Film(Lx, Ly, Lz, 1.0, 0.55, 3.0, 2, shape=shape)
+        g.init(ig.INIT_SLAB_Y, 0.01)
+        g.sweep(20, 10)
+        assert np.array_equal(g.read_series(), want), shape
+        assert np.array_equal(g.get_spins(), spins), shape
+        g.close()
 
 
-@pytest.mark.parametrize("shape", [ig.SHAPE_GRID_1, ig.SHAPE_GRID_2], ids=["grid1", "grid2"])
+@pytest.mark.parametrize("shape", [ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q], ids=["grid1", "grid2", "gridq"])
 @pytest.mark.parametrize("cold", [False, True], ids=["fast-table", "exact-table"])
 def test_mixed_batch_matches_films_run_alone(cold, shape):
     """cold: one film at T -> 0 (a reachable thr = 0 entry) and one at beta = 0
@@ -214,7 +217,7 @@ def test_shape_limits_and_switches():
     case = (12, 10, 40, ig.Y_GAPBC, ig.X_FREE, 0.55, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01)
     g, o = _pair(case)
     for shape, n, m in ((ig.SHAPE_RESIDENT, 7, 2), (ig.SHAPE_GRID_2, 5, 3), (ig.SHAPE_GRID_1, 4, 4),
-                        (ig.SHAPE_RESIDENT, 11, 1)):
+                        (ig.SHAPE_GRID_Q, 6, 2), (ig.SHAPE_RESIDENT, 11, 1)):
         g.set_shape(shape)
         g.sweep(n, m)
         assert np.array_equal(g.read_series(), o.sweep(n, m))
@@ -251,7 +254,7 @@ def test_batch_autotune_leaves_the_chains_alone():
     b = ig.Batch(specs)
     b.sweep(4, True)
     best = b.autotune()
-    assert best in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2) and b.get_shape() == best
+    assert best in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q) and b.get_shape() == best
     b.sweep(40, True)
     for i, sp in enumerate(specs):
         o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], replica=sp["replica"])
