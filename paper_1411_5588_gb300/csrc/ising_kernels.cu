@@ -13,7 +13,10 @@
 //  - init_kernel, pack_kernel, unpack_kernel, advance_kernel.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "ising_device.cuh"
+
 #include "ising_launch.h"
 
 namespace isg {
@@ -37,10 +40,41 @@ __device__ __forceinline__ void or_if_le(uint32_t& acc, uint32_t u, uint32_t t, 
       : "+r"(acc) : "r"(u), "r"(t), "r"(bit));
 }
 
+// The same with the bit as an immediate operand.
+template <uint32_t BIT>
+__device__ __forceinline__ void or_if_le_c(uint32_t& acc, uint32_t u, uint32_t t) {
+  asm("{\n\t.reg .pred p;\n\tsetp.le.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+      : "+r"(acc) : "r"(u), "r"(t), "n"(BIT));
+}
+template <uint32_t BIT>
+__device__ __forceinline__ void or_if_lt_c(uint32_t& acc, uint32_t u, uint32_t t) {
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+      : "+r"(acc) : "r"(u), "r"(t), "n"(BIT));
+}
+
 // acc | bit when u < t.
 __device__ __forceinline__ void or_if_lt(uint32_t& acc, uint32_t u, uint32_t t, uint32_t bit) {
   asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
       : "+r"(acc) : "r"(u), "r"(t), "r"(bit));
+}
+
+// Decisions of the sites at bits Q + 8I (Philox call Q, word u[I]) and
+// Q + 4 + 8I (call Q + 4, word v[I]) of a word.
+template <bool FAST, uint32_t Q, uint32_t I>
+__device__ __forceinline__ void site_pair(uint32_t& lt, const char* tb, uint32_t Y, uint32_t Y2, uint32_t u,
+                                          uint32_t v, bool two) {
+  uint32_t t, t2;
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(tb);
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(base + __byte_perm(Y, 0, 0x4440 + I)));
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t2) : "r"(base + __byte_perm(Y2, 0, 0x4440 + I)));
+  if (FAST) {
+    // table word thr - 1, or 0xFFFFFFFF for "always" (dE <= 0)
+    or_if_le_c<1u << (Q + 8 * I)>(lt, u, t);
+    if (two) or_if_le_c<1u << (Q + 4 + 8 * I)>(lt, v, t2);
+  } else {
+    or_if_lt_c<1u << (Q + 8 * I)>(lt, u, t);
+    if (two) or_if_lt_c<1u << (Q + 4 + 8 * I)>(lt, v, t2);
+  }
 }
 
 // Per-launch constants of one film, kept in registers.
@@ -162,38 +196,37 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const char* tb = reinterpret_cast<const char*>(s_thr);
   const PhiloxRow pr(row, c.sweep, X, c.rk0, c.rk1);
   uint32_t lt = 0;
-  // calls q and q + 4 are drawn together (two independent Philox chains)
-  auto calls = [&](uint32_t q, uint32_t Uq) {
-    if (FULL || q < ncalls) {
+  // calls Q and Q + 4 are drawn together (two independent Philox chains)
+  auto calls = [&](auto qc, uint32_t Uq) {
+    constexpr uint32_t Q = decltype(qc)::value;
+    if (FULL || Q < ncalls) {
       uint32_t u[4], v[4];
-      pr.draw2(8u * w + q, 8u * w + q + 4, u, v);
-      const bool two = FULL || q + 4 < ncalls;
+      pr.draw2(8u * w + Q, 8u * w + Q + 4, u, v);
+      const bool two = FULL || Q + 4 < ncalls;
       const uint32_t Y = ((Uq << 2) & 0x3C3C3C3Cu) | clsb;
       const uint32_t Y2 = ((Uq >> 2) & 0x3C3C3C3Cu) | clsb;
-#pragma unroll
-      for (uint32_t i = 0; i < 4; i++) {
-        if (FAST) {
-          // table word thr - 1, or 0xFFFFFFFF for "always" (dE <= 0); films
-          // with a reachable thr = 0 entry take the exact branch below
-          const uint32_t lo = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y, 0, 0x4440 + i));
-          const uint32_t lo2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y2, 0, 0x4440 + i));
-          or_if_le(lt, u[i], lo, 1u << (q + 8 * i));
-          if (two) or_if_le(lt, v[i], lo2, 1u << (q + 4 + 8 * i));
-        } else {
-          const uint32_t t = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y, 0, 0x4440 + i));
-          const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(Y2, 0, 0x4440 + i));
-          or_if_lt(lt, u[i], t, 1u << (q + 8 * i));
-          if (two) or_if_lt(lt, v[i], t2, 1u << (q + 4 + 8 * i));
-        }
-      }
+      site_pair<FAST, Q, 0>(lt, tb, Y, Y2, u[0], v[0], two);
+      site_pair<FAST, Q, 1>(lt, tb, Y, Y2, u[1], v[1], two);
+      site_pair<FAST, Q, 2>(lt, tb, Y, Y2, u[2], v[2], two);
+      site_pair<FAST, Q, 3>(lt, tb, Y, Y2, u[3], v[3], two);
     }
   };
+  using Q0 = std::integral_constant<uint32_t, 0>;
+  using Q1 = std::integral_constant<uint32_t, 1>;
+  using Q2 = std::integral_constant<uint32_t, 2>;
+  using Q3 = std::integral_constant<uint32_t, 3>;
   if (QUARTER) {
-    const uint32_t Uq = qsel == 0 ? U[0] : qsel == 1 ? U[1] : qsel == 2 ? U[2] : U[3];
-    calls(qsel, Uq);
+    switch (qsel) {
+      case 0: calls(Q0{}, U[0]); break;
+      case 1: calls(Q1{}, U[1]); break;
+      case 2: calls(Q2{}, U[2]); break;
+      default: calls(Q3{}, U[3]); break;
+    }
   } else {
-#pragma unroll
-    for (uint32_t q = 0; q < 4; q++) calls(q, U[q]);
+    calls(Q0{}, U[0]);
+    calls(Q1{}, U[1]);
+    calls(Q2{}, U[2]);
+    calls(Q3{}, U[3]);
   }
   const uint32_t valid = FULL ? 0xFFFFFFFFu : c.last_mask;
   return (lt | alw) & valid;
