@@ -290,6 +290,14 @@ int ising_gauss_legendre(int n, double a, double b, double *x, double *w);
 int ising_series_mean(const int64_t *records, size_t n, size_t stride, size_t col, size_t first,
                       double *mean);
 
+/* Eq. 1 from a record series (5 + Lx int64 per record): E[k] = -J B - H M
+ * - H1 M1 - Hn Mn with Hn = -H1, in binary64 from each record's integers (E
+ * may be NULL, else n doubles), and *mean (may be NULL) = the same
+ * combination of the column means over records first..n-1, each mean an
+ * exact integer sum and one division.  At least one output.  host. */
+int ising_series_energy(const int64_t *records, size_t n, int Lx, double J, double H, double H1, double *E,
+                        size_t first, double *mean);
+
 /* The film's own integral over its surface field: with Hn = -H1 written
  * into Eq. 1, dF/dH1 = -(M1 - Mn), so F(H1) - F(0) = -integral_0^{H1}
  * (m_1 - m_n) dH1' per wall site, from n Gauss-Legendre nodes on [0, H1];

@@ -26,6 +26,15 @@ def series_mean(records, col, first=0):
     return float(sum(vals)) / len(vals) if len(vals) < 2 ** 53 else sum(vals) / len(vals)
 
 
+def series_energy_mean(records, J, H, H1, first=0):
+    """Eq. 1 averaged over records[first:], from exact (Python integer)
+    column sums: -J <B> - H <M> - H1 <M1> - Hn <Mn>, Hn = -H1."""
+    r = np.asarray(records)[first:]
+    n = len(r)
+    B, M, M1, Mn = (sum(int(v) for v in r[:, c]) / n for c in (1, 2, 3, 4))
+    return -J * B - H * M - H1 * M1 + H1 * Mn
+
+
 def surface_field_ti(H1, m1, mn):
     """-integral_0^{H1} (m1 - mn) over Gauss-Legendre nodes on [0, H1]."""
     x, w = gauss_legendre(len(m1), 0.0, H1)

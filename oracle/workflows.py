@@ -57,10 +57,11 @@ def contact_angle(wl, records, gamma_pi2):
 
 def interface_tension(wl, records):
     first, betas = wl["first"], np.asarray(wl["betas"])
-    B = {role: OT.series_mean(rec, 1, first) for rec, role in zip(records, wl["roles"])}
+    U = {role: OT.series_energy_mean(rec, job["J"], 0.0, job["H1"], first)
+         for rec, job, role in zip(records, wl["jobs"], wl["roles"])}
     dF = []
     for s, _ in enumerate(wl["sizes"]):
-        dU = [-(B[("apbc", s, k)] - B[("pbc", s, k)]) for k in range(len(betas))]
+        dU = [U[("apbc", s, k)] - U[("pbc", s, k)] for k in range(len(betas))]
         dF.append(OA.ti_free_energy_beta(betas, dU, 0.0)[-1])
     L = np.array(wl["sizes"], dtype=np.float64)
     g, t = OA.fit_gamma_tau(L, L, dF)

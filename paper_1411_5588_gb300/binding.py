@@ -100,6 +100,7 @@ _SIGS = {
     "ising_gauss_legendre": [_c.c_int, _c.c_double, _c.c_double, P, P],
     "ising_series_mean": [P, _c.c_size_t, _c.c_size_t, _c.c_size_t, _c.c_size_t, DP],
     "ising_ti_surface_field": [_c.c_int, _c.c_double, P, P, DP],
+    "ising_series_energy": [P, _c.c_size_t, _c.c_int, _c.c_double, _c.c_double, _c.c_double, P, _c.c_size_t, DP],
     "ising_ti_beta_trapezoid": [_c.c_int, P, P, DP],
     "ising_ti_temperature_trapezoid": [_c.c_int, P, P, DP],
     "ising_ti_young_difference": [_c.c_int, _c.c_double, P, P, DP],
@@ -440,6 +441,16 @@ def series_mean(records, col, first=0):
     check(lib().ising_series_mean(_ptr(r), r.shape[0], r.shape[1], int(col), int(first), _c.byref(out)),
           "ising_series_mean")
     return out.value
+
+
+def series_energy(records, J, H1, H=0.0, first=0):
+    """Eq. 1 per record and the mean over records[first:] (exact integer sums)."""
+    r = np.ascontiguousarray(records, dtype=np.int64)
+    E = np.zeros(r.shape[0])
+    mean = _c.c_double()
+    check(lib().ising_series_energy(_ptr(r), r.shape[0], r.shape[1] - 5, float(J), float(H), float(H1), _ptr(E),
+                                    int(first), _c.byref(mean)), "ising_series_energy")
+    return E, mean.value
 
 
 def ti_surface_field(H1, m1, mn):

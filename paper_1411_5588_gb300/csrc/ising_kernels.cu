@@ -339,9 +339,10 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // Half-sweep of every film of a launch: block b handles words_per_block(ITEMS)
 // words of film owner[b], whose descriptor is staged in shared memory.  FAST:
 // no film of the launch has a reachable thr = 0 entry (the compare-only
-// table); otherwise every film takes the exact variant.
+// table); otherwise every film takes the exact variant (which, at two words
+// per thread, needs the registers of one block per SM fewer).
 template <bool FAST, uint32_t ITEMS>
-__global__ void __launch_bounds__(kFilmThreads, kMultiMinBlocks)
+__global__ void __launch_bounds__(kFilmThreads, (FAST || ITEMS < 2) ? kMultiMinBlocks : kMultiMinBlocks - 1)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k) {
   constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;

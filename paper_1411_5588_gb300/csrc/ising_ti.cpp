@@ -58,6 +58,32 @@ int ising_series_mean(const int64_t* records, size_t n, size_t stride, size_t co
   return ISING_OK;
 }
 
+int ising_series_energy(const int64_t* records, size_t n, int Lx, double J, double H, double H1, double* E,
+                        size_t first, double* mean) {
+  clear_error();
+  if (!records || Lx < 1 || (!E && !mean) || (mean && first >= n)) return fail(ISING_EINVAL, "series_energy: bad arguments");
+  const size_t stride = 5 + (size_t)Lx;
+  // Eq. 1 with Hn = -H1, term by term from the record's integers
+  if (E)
+    for (size_t k = 0; k < n; k++) {
+      const int64_t* r = records + k * stride;
+      E[k] = -J * (double)r[1] - H * (double)r[2] - H1 * (double)r[3] + H1 * (double)r[4];
+    }
+  if (mean) {
+    __int128 sB = 0, sM = 0, s1 = 0, sn = 0;
+    for (size_t k = first; k < n; k++) {
+      const int64_t* r = records + k * stride;
+      sB += r[1];
+      sM += r[2];
+      s1 += r[3];
+      sn += r[4];
+    }
+    const double c = (double)(n - first);
+    *mean = -J * ((double)sB / c) - H * ((double)sM / c) - H1 * ((double)s1 / c) + H1 * ((double)sn / c);
+  }
+  return ISING_OK;
+}
+
 int ising_ti_surface_field(int n, double H1, const double* m1, const double* mn, double* delta_f1) {
   clear_error();
   if (n < 1 || !m1 || !mn || !delta_f1) return fail(ISING_EINVAL, "ti_surface_field: bad arguments");

@@ -21,7 +21,7 @@ import math
 import numpy as np
 
 from . import analysis as A
-from .binding import Batch, series_mean, ti_surface_field
+from .binding import Batch, series_energy, series_mean, ti_surface_field
 
 
 def run(workload, use_graph=True):
@@ -74,13 +74,12 @@ def contact_angle(wl, records, gamma_pi2):
 
 def interface_tension(wl, records):
     first, betas, sizes = wl["first"], np.asarray(wl["betas"]), wl["sizes"]
-    B = {}
-    for rec, role in zip(records, wl["roles"]):
-        B[role] = series_mean(rec, 1, first)
+    U = {}
+    for rec, job, role in zip(records, wl["jobs"], wl["roles"]):
+        U[role] = series_energy(rec, job["J"], job["H1"], first=first)[1]  # <E> of Eq. 1
     dF = []
     for s, L in enumerate(sizes):
-        # U = <E> = -J <B> with H = H1 = 0
-        dU = np.array([-(B[("apbc", s, k)] - B[("pbc", s, k)]) for k in range(len(betas))])
+        dU = np.array([U[("apbc", s, k)] - U[("pbc", s, k)] for k in range(len(betas))])
         dF.append(A.ti_free_energy_beta(betas, dU, 0.0)[-1])
     L = np.array(sizes, dtype=np.float64)
     gamma_pi2, tau0 = A.fit_gamma_tau(L, L, dF)

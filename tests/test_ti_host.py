@@ -65,3 +65,23 @@ def test_series_mean_is_exact():
     assert ig.series_mean(big, 0) == want
     assert OT.series_mean(big, 0) == want
     assert ig.series_mean(big, 1, first=1) == 14 / 3
+
+
+def test_series_energy_matches_the_oracle_film_energy():
+    """Eq. 1 from the records (product C, exact integer column sums) against
+    the oracle's own energy of the lattice after every sweep, and the mean
+    against the oracle's numpy restatement."""
+    from oracle import oracle as O
+    for ym, H, H1 in ((O.Y_GAPBC, 0.0, 0.55), (O.Y_PBC, 0.1, -0.3), (O.Y_APBC, -0.2, 0.0)):
+        f = O.Film(5, 6, 10, 1.3, H1, 2.7, 4, y_mode=ym, H=H)
+        f.init(O.INIT_RANDOM)
+        recs, want = [], []
+        for _ in range(12):
+            recs.append(f.sweep(1, 1)[0])
+            want.append(f.energy())
+        recs = np.array(recs)
+        E, mean = ig.series_energy(recs, 1.3, H1, H=H, first=2)
+        assert np.allclose(E, want, rtol=1e-14, atol=1e-12)
+        m = OT.series_energy_mean(recs, 1.3, H, H1, 2)
+        assert abs(mean - m) <= 1e-12 * max(1.0, abs(m))
+        assert abs(mean - np.mean(want[2:])) <= 1e-12 * max(1.0, abs(m))
