@@ -216,11 +216,29 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   using Q2 = std::integral_constant<uint32_t, 2>;
   using Q3 = std::integral_constant<uint32_t, 3>;
   if (QUARTER) {
-    switch (qsel) {
-      case 0: calls(Q0{}, U[0]); break;
-      case 1: calls(Q1{}, U[1]); break;
-      case 2: calls(Q2{}, U[2]); break;
-      default: calls(Q3{}, U[3]); break;
+    // one code path for the four lanes (a switch on qsel would run all four
+    // bodies one after another): runtime call index, bit in a register
+    const uint32_t Uq = qsel == 0 ? U[0] : qsel == 1 ? U[1] : qsel == 2 ? U[2] : U[3];
+    if (FULL || qsel < ncalls) {
+      uint32_t u[4], v[4];
+      pr.draw2(8u * w + qsel, 8u * w + qsel + 4, u, v);
+      const bool two = FULL || qsel + 4 < ncalls;
+      const uint32_t Y = ((Uq << 2) & 0x3C3C3C3Cu) | clsb;
+      const uint32_t Y2 = ((Uq >> 2) & 0x3C3C3C3Cu) | clsb;
+      const uint32_t base = (uint32_t)__cvta_generic_to_shared(tb);
+#pragma unroll
+      for (uint32_t i = 0; i < 4; i++) {
+        uint32_t t, t2;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(base + __byte_perm(Y, 0, 0x4440 + i)));
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t2) : "r"(base + __byte_perm(Y2, 0, 0x4440 + i)));
+        if (FAST) {
+          or_if_le(lt, u[i], t, 1u << (qsel + 8 * i));
+          if (two) or_if_le(lt, v[i], t2, 1u << (qsel + 4 + 8 * i));
+        } else {
+          or_if_lt(lt, u[i], t, 1u << (qsel + 8 * i));
+          if (two) or_if_lt(lt, v[i], t2, 1u << (qsel + 4 + 8 * i));
+        }
+      }
     }
   } else {
     calls(Q0{}, U[0]);
@@ -898,8 +916,8 @@ cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_byt
   if (n_films == 0 || n_sweeps == 0) return cudaSuccess;
   if (smem_bytes > kResidentMaxSmem || threads == 0 || threads > kResidentThreads || threads % 32u)
     return cudaErrorInvalidValue;
-  if (exact) return launch_pdl(resident_kernel<false>, n_films, threads, smem_bytes, st, films, pool, records, n_sweeps);
-  return launch_pdl(resident_kernel<true>, n_films, threads, smem_bytes, st, films, pool, records, n_sweeps);
+  auto* kern = exact ? resident_kernel<false> : resident_kernel<true>;
+  return launch_pdl(kern, n_films, threads, smem_bytes, st, films, pool, records, n_sweeps);
 }
 
 int update_blocks_per_sm() {
