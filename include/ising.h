@@ -175,6 +175,18 @@ typedef struct {
 } ising_obs;
 int ising_measure(ising *h, ising_obs *out);
 
+/* Asynchronous drain: enqueue the copy of up to cap pending records (oldest
+ * first, 5 + Lx int64 each) into host memory buf on cuda_stream (a
+ * cudaStream_t as void*; NULL = a copy stream of the handle), ordered after
+ * all work enqueued on the handle so far, so that it overlaps the sweeps
+ * enqueued next.  buf should be pinned (page-locked) for the copy to be
+ * asynchronous; it must stay valid until the copy completes, which it has
+ * once that stream reaches this point (synchronise it, or the handle with
+ * ising_synchronize after ising_read_series).  *n_records receives the count;
+ * those records count as read.  Later sweeps never overwrite ring slots
+ * still being copied, and growing the ring waits for the copy. */
+int ising_read_series_async(ising *h, int64_t *buf, size_t cap, size_t *n_records, void *cuda_stream);
+
 /* Drain up to cap pending records (5 + Lx int64 each, oldest first) into
  * host memory buf; *n_records receives the number copied.  Synchronises. */
 int ising_read_series(ising *h, int64_t *buf, size_t cap, size_t *n_records);

@@ -59,6 +59,7 @@ _SIGS = {
     "ising_set_options": [P, _c.c_int, _c.c_int, _c.c_double, _c.c_uint32],
     "ising_set_shape": [P, _c.c_int],
     "ising_reserve_records": [P, _c.c_uint64],
+    "ising_read_series_async": [P, P, _c.c_size_t, _c.POINTER(_c.c_size_t), P],
     "ising_batch_reserve_records": [P, _c.c_uint64],
     "ising_get_shape": [P, _c.c_uint32, _c.POINTER(_c.c_int)],
     "ising_autotune": [P, _c.c_uint32, _c.POINTER(_c.c_int)],
@@ -190,6 +191,16 @@ class Film:
 
     def reserve_records(self, n):
         check(lib().ising_reserve_records(self._h, int(n)), "ising_reserve_records")
+
+    def read_series_async(self, host_ptr, cap, stream=None):
+        """Enqueue the copy of up to cap pending records to host memory at
+        host_ptr (pinned, (cap, 5 + Lx) int64) on stream (torch stream or
+        None for the handle's copy stream); returns the count."""
+        n = _c.c_size_t()
+        s = _torch_stream(stream) if stream is not None else None
+        check(lib().ising_read_series_async(self._h, P(int(host_ptr)), int(cap), _c.byref(n), s),
+              "ising_read_series_async")
+        return n.value
 
     def get_shape(self, measure_every):
         v = _c.c_int()

@@ -254,6 +254,13 @@ struct ising {
   int8_t* d_stage = nullptr;
   bool dirty = true;
   int shape = ISING_SHAPE_AUTO;
+  // asynchronous record copies (ising_read_series_async): records
+  // [inflight_lo, inflight_hi) of the ring counters are still being copied
+  // on copy_stream until ev_copied
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_copied = nullptr;
+  bool inflight = false;
+  uint64_t inflight_lo = 0, inflight_hi = 0;
   FilmDesc& d() { return fs.h[0]; }
 };
 
@@ -289,6 +296,10 @@ int ensure_ring(ising* h, uint64_t extra) {
   FilmDesc& d = h->d();
   const uint64_t pending = h->rec_written - h->rec_read;
   if (pending + extra <= d.rec_cap) return ISING_OK;
+  if (h->inflight) {  // the old ring is about to be freed
+    ISG_CK(cudaEventSynchronize(h->ev_copied));
+    h->inflight = false;
+  }
   uint64_t cap = std::max<uint64_t>({64, 2 * (uint64_t)d.rec_cap, pending + extra});
   if (cap > 0xFFFFFFF0ull) return fail(ISING_ENOMEM, "record series too long; read it out first");
   const size_t rl = record_len(d);
@@ -580,6 +591,11 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
   const uint64_t nrec = measure_every ? (s0 + n) / measure_every - s0 / measure_every : 0;
   int rc = ensure_ring(h, nrec);
   if (rc) return rc;
+  // records of this call land on ring slots of records rec_written + nrec -
+  // rec_cap and later: if any of those are still being copied out, wait
+  if (h->inflight && cudaEventQuery(h->ev_copied) == cudaSuccess) h->inflight = false;
+  if (h->inflight && nrec && h->rec_written + nrec > h->inflight_lo + d.rec_cap)
+    ISG_CK(cudaStreamWaitEvent(h->fs.stream, h->ev_copied, 0));
   rc = sync_desc(h);
   if (rc) return rc;
   const int shape = resolve_shape(h, measure_every);
@@ -652,6 +668,42 @@ int ising_read_series(ising* h, int64_t* buf, size_t cap, size_t* n_records) {
   return ISING_OK;
 }
 
+int ising_read_series_async(ising* h, int64_t* buf, size_t cap, size_t* n_records, void* cuda_stream) {
+  clear_error();
+  if (!h || !n_records || (cap && !buf)) return fail(ISING_EINVAL, "NULL argument");
+  cudaStream_t cs = (cudaStream_t)cuda_stream;
+  if (!cs) {
+    if (!h->copy_stream) ISG_CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    cs = h->copy_stream;
+  }
+  if (!h->ev_ready) ISG_CK(cudaEventCreateWithFlags(&h->ev_ready, cudaEventDisableTiming));
+  if (!h->ev_copied) ISG_CK(cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming));
+  const FilmDesc& d = h->d();
+  const size_t rl = record_len(d);
+  const uint64_t k = std::min<uint64_t>(h->rec_written - h->rec_read, cap);
+  *n_records = (size_t)k;
+  if (k == 0) return ISING_OK;
+  if (h->inflight && cudaEventQuery(h->ev_copied) == cudaSuccess) h->inflight = false;
+  // the copy starts once everything enqueued on the handle so far is done
+  ISG_CK(cudaEventRecord(h->ev_ready, h->fs.stream));
+  ISG_CK(cudaStreamWaitEvent(cs, h->ev_ready, 0));
+  if (h->inflight) ISG_CK(cudaStreamWaitEvent(cs, h->ev_copied, 0));  // one in-flight range at a time
+  uint64_t i = 0;
+  while (i < k) {
+    const uint64_t slot = (h->rec_read + i) % d.rec_cap;
+    const uint64_t run = std::min<uint64_t>(k - i, d.rec_cap - slot);
+    ISG_CK(cudaMemcpyAsync(buf + i * rl, h->fs.rec + d.rec_off + slot * rl, run * rl * sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, cs));
+    i += run;
+  }
+  ISG_CK(cudaEventRecord(h->ev_copied, cs));
+  h->inflight_lo = h->inflight ? h->inflight_lo : h->rec_read;
+  h->inflight_hi = h->rec_read + k;
+  h->inflight = true;
+  h->rec_read += k;
+  return ISING_OK;
+}
+
 int ising_pending_records(const ising* h, size_t* n) {
   clear_error();
   if (!h || !n) return fail(ISING_EINVAL, "NULL argument");
@@ -667,6 +719,10 @@ int ising_synchronize(ising* h, double timeout_s) {
 
 int ising_destroy(ising* h) {
   if (!h) return ISING_OK;
+  if (h->ev_copied) cudaEventSynchronize(h->ev_copied);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->ev_ready) cudaEventDestroy(h->ev_ready);
+  if (h->ev_copied) cudaEventDestroy(h->ev_copied);
   h->fs.release();
   if (h->d_direct) cudaFree(h->d_direct);
   if (h->d_stage) cudaFree(h->d_stage);

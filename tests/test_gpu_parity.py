@@ -262,3 +262,33 @@ def test_batch_autotune_leaves_the_chains_alone():
         assert np.array_equal(b.read_series(i), o.sweep(44, 2))
         assert np.array_equal(b.get_spins(i), o.get_spins())
     b.close()
+
+
+def test_async_record_reads_match_the_oracle():
+    """ising_read_series_async: one record per step copied to pinned host
+    memory while later steps run (through several wraps of the 64-record
+    ring), then a ring growth with a copy still in flight, then synchronous
+    reads; every record equals the oracle's."""
+    torch = pytest.importorskip("torch")
+    case = (6, 8, 40, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01)
+    for shape in (ig.SHAPE_RESIDENT, ig.SHAPE_GRID_1):
+        g, o = _pair(case, shape=shape)
+        rl = 5 + case[0]
+        host = torch.zeros((300, rl), dtype=torch.int64).pin_memory()
+        n = 0
+        for i in range(150):
+            g.sweep(2, 2)
+            n += g.read_series_async(host[n].data_ptr(), 1)
+        assert n == 150
+        g.sweep(20, 1)
+        k = g.read_series_async(host[150].data_ptr(), 10)  # in flight while the ring grows below
+        g.sweep(300, 1)
+        rest = g.read_series()
+        g.synchronize()
+        want = o.sweep(300, 2)
+        assert np.array_equal(host[:150].numpy(), want)
+        want = np.concatenate([o.sweep(20, 1), o.sweep(300, 1)])
+        assert k == 10 and np.array_equal(host[150:160].numpy(), want[:10])
+        assert np.array_equal(rest, want[10:])
+        assert np.array_equal(g.get_spins(), o.get_spins())
+        g.close()
