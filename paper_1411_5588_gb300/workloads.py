@@ -26,9 +26,12 @@ The three film sets of the paper's procedures (Secs. II B, II C, III, IV);
                         n_gl Gauss-Legendre nodes of [0, H1] ("node")
   interface_tension_set per size Lx = Lz and per beta on a grid from 0.2:
                         antiperiodic ("apbc") and periodic ("pbc") y, H1 = 0
+                        (default sizes: Fig. 12's Lx = Lz = 20..50, Ly = 60)
   line_tension_set      per size of a constant-area set (Lx Lz and Ly Lz
                         fixed): films with the Eq. 11 boundary ("interface")
                         and periodic-y films ("plus") at the nodes of [0, H1]
+                        (default: Fig. 13's Lx Lz = 1536, Ly Lz = 9216 with
+                        Lz = 16..96 at H1 = 0.45)
 """
 from __future__ import annotations
 
@@ -123,7 +126,7 @@ def contact_angle_set(Lx=32, Ly=96, Lz=64, T=3.0, H1s=(0.15, 0.3, 0.45, 0.55), n
                 n_sweeps=n_sweeps, first=first, jobs=jobs, roles=roles)
 
 
-def interface_tension_set(sizes=(20, 30, 40), Ly=60, T=3.0, beta0=0.2, n_beta=24, n_sweeps=2000, first=500,
+def interface_tension_set(sizes=(20, 30, 40, 50), Ly=60, T=3.0, beta0=0.2, n_beta=24, n_sweeps=2000, first=500,
                           seed=8):
     betas = np.linspace(beta0, 1.0 / T, n_beta)
     jobs, roles = [], []
@@ -136,8 +139,8 @@ def interface_tension_set(sizes=(20, 30, 40), Ly=60, T=3.0, beta0=0.2, n_beta=24
                 first=first, jobs=jobs, roles=roles)
 
 
-def line_tension_set(sizes=((32, 128, 16), (16, 64, 32), (8, 32, 64)), T=3.0, H1=0.45, n_gl=8, n_sweeps=2000,
-                     first=500, seed=9):
+def line_tension_set(sizes=((96, 576, 16), (48, 288, 32), (32, 192, 48), (24, 144, 64), (16, 96, 96)), T=3.0,
+                     H1=0.45, n_gl=8, n_sweeps=2000, first=500, seed=9):
     jobs, roles = [], []
     for s, (Lx, Ly, Lz) in enumerate(sizes):
         for i, x in enumerate(_nodes(n_gl, 0.0, H1)):
