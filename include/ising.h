@@ -417,6 +417,16 @@ int ising_step_free_energy(int n, const double *theta, const double *gamma, doub
  * f_s > 0. */
 int ising_roughening_fs_fit(int n, const double *T, const double *f_s, double T_R, double *A, double *log_amp);
 
+/* Sec. III C: the critical field H1* below which the contact angle stays at
+ * pi/2, from a scan (H1[i] strictly increasing, theta[i]), n >= 2: the
+ * first point whose tilt pi/2 - theta exceeds tol, and the crossing of
+ * tol on the line through it and the point before.  f_s = 2 H1* +
+ * T ln(Lx) / Lz (Eq. 32 solved for f_s; the paper's f_s = 2 H1* as
+ * Lz -> infinity).  EINVAL when the tilt does not cross tol inside the scan
+ * (or already at its first point). */
+int ising_critical_field(int n, const double *H1, const double *theta, double tol, double T, double Lx, double Lz,
+                         double *h1_star, double *f_s);
+
 /* Eqs. 28-32, the single-step model: phi = <pi/2 - theta> =
  * (W+1 - W-1) / (Lx Z) with W0 = 1, W+-1 = Lx exp(-f_s Lz / T)
  * exp(+-2 H1 Lz / T), evaluated relative to the largest weight (no

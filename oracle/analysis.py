@@ -16,11 +16,12 @@ Each function follows one passage:
   Eq. 20   dF / (Lz Lx) = gamma(pi/2) + (2 / Lx) tau(0, pi/2)
   Eq. 21   solved for 2 Lz [tau(H1, theta) - tau(0, pi/2)]
   Eqs. 23-25, 26-27, 28-32  stiffness, roughening fits, step model
+  Sec. III C              the critical field H1* and f_s from Eq. 32
 
 Fits use numpy's least-squares routine (``np.linalg.lstsq``) as a library
-step.  Parity unpinned: none; every function is pinned in
-tests/test_oracle_analysis.py (closed forms, exact enumeration, the T = 0
-limits).
+step.  Every function is pinned in tests/test_oracle_analysis.py (closed
+forms, exact enumeration, Kaufman's torus, the T = 0 limits, the step
+model), so none is parity-unpinned.
 """
 from __future__ import annotations
 
@@ -143,6 +144,20 @@ def roughening_fs_fit(T, f_s, T_R):
     x = (1.0 - np.asarray(T, dtype=np.float64) / T_R) ** -0.5
     log_amp, slope = _lsq([np.ones_like(x), x], np.log(np.asarray(f_s, dtype=np.float64)))
     return -float(slope), float(log_amp)
+
+
+def critical_field(H1, theta, tol, T, Lx, Lz):
+    """Sec. III C: the tilt pi/2 - theta first exceeds tol between two scan
+    points; H1* is where their straight line crosses tol.  Eq. 32 solved for
+    f_s gives f_s = 2 H1* + T ln(Lx) / Lz."""
+    H1 = np.asarray(H1, dtype=np.float64)
+    tilt = math.pi / 2 - np.asarray(theta, dtype=np.float64)
+    above = np.nonzero(tilt > tol)[0]
+    i = int(above[0])
+    if i == 0:
+        raise ValueError("tilt above tol at the first point")
+    h = H1[i - 1] + (tol - tilt[i - 1]) * (H1[i] - H1[i - 1]) / (tilt[i] - tilt[i - 1])
+    return float(h), 2.0 * float(h) + T * math.log(Lx) / Lz
 
 
 def step_model(H1, f_s, T, Lx, Lz):

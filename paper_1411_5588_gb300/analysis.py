@@ -146,6 +146,15 @@ def roughening_fs_fit(T, f_s, T_R):
     return A.value, a.value
 
 
+def critical_field(H1, theta, tol, T, Lx, Lz):
+    """Sec. III C and Eq. 32: returns (H1*, f_s)."""
+    h, t = _f64(H1), _f64(theta)
+    a, b = _out(), _out()
+    check(lib().ising_critical_field(h.size, _ptr(h), _ptr(t), float(tol), float(T), float(Lx), float(Lz),
+                                     _c.byref(a), _c.byref(b)), "ising_critical_field")
+    return a.value, b.value
+
+
 def step_model(H1, f_s, T, Lx, Lz):
     """Eqs. 28-32: returns (phi, h1_star)."""
     p, h = _out(), _out()

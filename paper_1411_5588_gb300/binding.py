@@ -119,6 +119,7 @@ _SIGS = {
     "ising_step_free_energy": [_c.c_int, P, P, DP, DP],
     "ising_roughening_fs_fit": [_c.c_int, P, P, _c.c_double, DP, DP],
     "ising_step_model": [_c.c_double] * 5 + [DP, DP],
+    "ising_critical_field": [_c.c_int, P, P] + [_c.c_double] * 4 + [DP, DP],
     "ising_measure_packed_noalloc": [P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64, P, P],
     "ising_strerror": [_c.c_int],
     "ising_last_error": [],

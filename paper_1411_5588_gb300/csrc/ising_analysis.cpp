@@ -267,4 +267,23 @@ int ising_step_model(double H1, double f_s, double T, double Lx, double Lz, doub
   return ISING_OK;
 }
 
+int ising_critical_field(int n, const double* H1, const double* theta, double tol, double T, double Lx, double Lz,
+                         double* h1_star, double* f_s) {
+  clear_error();
+  if (n < 2 || !H1 || !theta || !h1_star || !f_s || !(tol > 0) || !(T > 0) || !(Lx > 0) || !(Lz > 0))
+    return fail(ISING_EINVAL, "critical_field: bad arguments");
+  for (int i = 1; i < n; i++)
+    if (!(H1[i] > H1[i - 1])) return fail(ISING_EINVAL, "critical_field: H1 must increase");
+  // Sec. III C: the first point whose tilt pi/2 - theta exceeds tol; H1* is
+  // where the straight line through it and the point before crosses tol
+  const double half_pi = 0.5 * M_PI;
+  int i = 0;
+  while (i < n && half_pi - theta[i] <= tol) i++;
+  if (i == 0 || i == n) return fail(ISING_EINVAL, "critical_field: the tilt does not cross tol inside the scan");
+  const double p0 = half_pi - theta[i - 1], p1 = half_pi - theta[i];
+  *h1_star = H1[i - 1] + (tol - p0) * (H1[i] - H1[i - 1]) / (p1 - p0);
+  *f_s = 2.0 * *h1_star + T * std::log(Lx) / Lz;  // Eq. 32 solved for f_s
+  return ISING_OK;
+}
+
 }  // extern "C"

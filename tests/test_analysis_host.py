@@ -141,3 +141,15 @@ def test_bad_arguments_are_einval():
         with pytest.raises(ig.IsingError) as e:
             f()
         assert e.value.status == ig.EINVAL
+
+
+def test_critical_field(rng):
+    H1 = np.linspace(0.05, 0.8, 31)
+    tilt = np.where(H1 < 0.4, 1e-4 * rng.random(31), (H1 - 0.4) * 0.9)
+    theta = math.pi / 2 - tilt
+    a = A.critical_field(H1, theta, 0.01, 2.0, 64, 128)
+    b = OA.critical_field(H1, theta, 0.01, 2.0, 64, 128)
+    assert close(a, b)
+    for bad in ((H1, np.full(31, math.pi / 2)), (H1[::-1].copy(), theta)):
+        with pytest.raises(ig.IsingError):
+            A.critical_field(bad[0], bad[1], 0.01, 2.0, 64, 128)

@@ -348,3 +348,18 @@ def test_step_model_limits():
     assert abs(phi - (1 - Wm) / (2 + Wm) / Lx) < 1e-15
     phi, _ = OA.step_model(1.0, fs, T, Lx, Lz)
     assert abs(phi - 1 / Lx) < 1e-6 / Lx
+
+
+def test_critical_field_recovers_the_step_model_onset():
+    """Sec. III C: theta(H1) drawn from the single-step model (Eqs. 28-31)
+    with a known f_s; at H1* of Eq. 32 the up-step weight equals the flat
+    one, so the tilt there is (1 - W-1)/((2 + W-1) Lx), and the crossing of
+    that tilt gives back H1* and f_s (to the scan's resolution)."""
+    fs, T, Lx, Lz = 1.1, 1.5, 48, 64
+    hs = 0.5 * fs - T * math.log(Lx) / (2 * Lz)
+    Wm = Lx * math.exp(-fs * Lz / T - 2 * hs * Lz / T)
+    tol = (1 - Wm) / (2 + Wm) / Lx
+    H1 = np.linspace(0.0, 0.6, 2401)
+    theta = np.array([math.pi / 2 - OA.step_model(h, fs, T, Lx, Lz)[0] for h in H1])
+    h, f = OA.critical_field(H1, theta, tol, T, Lx, Lz)
+    assert abs(h - hs) < 1e-4 and abs(f - fs) < 2e-4
