@@ -247,6 +247,9 @@ int ising_batch_autotune(ising_batch *b, int *shape);
 /* Per-film accessors (index i < n).  Host buffers; synchronise. */
 int ising_batch_get_spins(ising_batch *b, size_t i, int8_t *s);
 int ising_batch_read_series(ising_batch *b, size_t i, int64_t *buf, size_t cap, size_t *n_records);
+/* Records of film i enqueued so far and not yet read (host counter; does not
+ * synchronise). */
+int ising_batch_pending_records(const ising_batch *b, size_t i, size_t *n);
 int ising_batch_synchronize(ising_batch *b, double timeout_s);
 int ising_batch_destroy(ising_batch *b);
 

@@ -90,6 +90,7 @@ _SIGS = {
     "ising_batch_get_spins": [P, _c.c_size_t, P],
     "ising_batch_read_series": [P, _c.c_size_t, P, _c.c_size_t, _c.POINTER(_c.c_size_t)],
     "ising_batch_synchronize": [P, _c.c_double],
+    "ising_batch_pending_records": [P, _c.c_size_t, _c.POINTER(_c.c_size_t)],
     "ising_batch_destroy": [P],
     "ising_server_create": [_c.c_size_t, _c.c_uint32, _c.POINTER(P)],
     "ising_batch_submit": [P, _c.POINTER(IsingJob), _c.c_size_t, _c.POINTER(_c.c_uint64)],
@@ -372,9 +373,16 @@ class Batch:
         check(lib().ising_batch_get_spins(self._h, int(i), _ptr(a)), "ising_batch_get_spins")
         return a
 
-    def read_series(self, i, cap=1 << 20):
+    def pending_records(self, i):
+        n = _c.c_size_t()
+        check(lib().ising_batch_pending_records(self._h, int(i), _c.byref(n)), "ising_batch_pending_records")
+        return n.value
+
+    def read_series(self, i, cap=None):
         rl = 5 + int(self.specs[i]["Lx"])
-        buf = np.zeros((cap, rl), dtype=np.int64)
+        if cap is None:
+            cap = self.pending_records(i)
+        buf = np.zeros((max(cap, 1), rl), dtype=np.int64)
         n = _c.c_size_t()
         check(lib().ising_batch_read_series(self._h, int(i), _ptr(buf), int(cap), _c.byref(n)),
               "ising_batch_read_series")

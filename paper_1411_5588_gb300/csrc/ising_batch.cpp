@@ -370,6 +370,14 @@ int ising_batch_read_series(ising_batch* b, size_t i, int64_t* buf, size_t cap, 
   return ISING_OK;
 }
 
+int ising_batch_pending_records(const ising_batch* b, size_t i, size_t* n) {
+  clear_error();
+  if (!b || !n) return fail(ISING_EINVAL, "NULL argument");
+  if (i >= b->fs.h.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
+  *n = (size_t)(b->rec_written[i] - b->rec_read[i]);
+  return ISING_OK;
+}
+
 int ising_batch_synchronize(ising_batch* b, double timeout_s) {
   clear_error();
   if (!b) return fail(ISING_EINVAL, "NULL batch");
