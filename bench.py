@@ -31,6 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+def alu_frac(attempts_per_ns):
+    """Fraction of the update kernels' ALU roofline (OPS_PER_ATTEMPT int32 ops
+    per attempt against 152 SMs x 128 lanes x 2.07 GHz)."""
+    return attempts_per_ns * OPS_PER_ATTEMPT / (N_SM * LANES_PER_SM * SM_MAX_GHZ)
+
+
 SHAPE_NAMES = {0: "auto", 1: "resident", 2: "grid, 1 word/thread", 3: "grid, 2 words/thread",
                4: "grid, 4 threads/word"}
 SHAPE_FLAGS = {1: "resident", 2: "grid1", 3: "grid2", 4: "gridq"}
@@ -231,6 +237,7 @@ def batched_vs_plain(ig, WL, torch, sweeps=20):
     plain = per_sweep * sweeps / tp / 1e9
     return {"workload": "64 films 32x64x128..96x192x384 (16 H1 nodes x 2 T x 2 seeds), records every 10 sweeps",
             "batched": batched, "plain": plain, "ratio": batched / plain, "unit": UNIT, "batched_shape": shape,
+            "batched_alu_frac": alu_frac(batched),
             "note": "both sides autotuned (library autotuner) before timing",
             "sweeps": {"batched": 2 * sweeps, "plain_per_film": sweeps}}
 
@@ -326,8 +333,9 @@ def t_scan_slice(ig, WL, sweeps=4):
     b.synchronize()
     dt = time.perf_counter() - t0
     b.close()
+    a = sum(WL.sites(j) for j in jobs) * sweeps / dt / 1e9
     return {"workload": f"40 films 120x240x1600 (T = 1.5..4.4), {sweeps} sweeps with a record every sweep",
-            "attempts_per_ns": sum(WL.sites(j) for j in jobs) * sweeps / dt / 1e9, "wall_s": dt}
+            "attempts_per_ns": a, "alu_frac": alu_frac(a), "wall_s": dt}
 
 
 def procedures(ig, WL):
@@ -354,7 +362,7 @@ def procedures(ig, WL):
         b.close()
         att = sum(WL.sites(j) for j in wl["jobs"]) * wl["n_sweeps"]
         return recs, {"films": len(wl["jobs"]), "attempts": att, "sweep_s": dt, "attempts_per_ns": att / dt / 1e9,
-                      "shape": shape}
+                      "alu_frac": alu_frac(att / dt / 1e9), "shape": shape}
 
     out = {}
     it = WL.interface_tension_set()
