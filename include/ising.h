@@ -464,6 +464,15 @@ int ising_measure_packed_noalloc(const uint32_t *spins, int Lx, int Ly, int Lz, 
 
 /* ------------------------------------------------------------- misc */
 
+/* Bounds checking.  A library built with ISING_CHECKED tests every lattice
+ * word index of the update, resident and record kernels against its plane:
+ * an out-of-range index is counted and the first one kept (site id << 48 |
+ * index), and the access is redirected (a load reads word 0, a store is
+ * dropped) -- nothing traps.  *checked = 1 for such a build, with the totals
+ * of the process so far; other builds give *checked = 0 and zeros.
+ * ECUDA if the counters cannot be read. */
+int ising_check_counters(int *checked, uint64_t *count, uint64_t *first);
+
 const char *ising_strerror(int status);
 const char *ising_last_error(void);
 /* Library version and the compute capability it was built for (e.g. 103). */

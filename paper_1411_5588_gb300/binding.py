@@ -122,6 +122,7 @@ _SIGS = {
     "ising_step_model": [_c.c_double] * 5 + [DP, DP],
     "ising_critical_field": [_c.c_int, P, P] + [_c.c_double] * 4 + [DP, DP],
     "ising_measure_packed_noalloc": [P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64, P, P],
+    "ising_check_counters": [_c.POINTER(_c.c_int), _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64)],
     "ising_strerror": [_c.c_int],
     "ising_last_error": [],
     "ising_version": [_c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)],
@@ -447,6 +448,13 @@ class Server:
 
 
 # ------------------------------------------------------------- host FP64
+
+def check_counters():
+    """(checked build?, out-of-range accesses so far, the first one)."""
+    c, n, f = _c.c_int(), _c.c_uint64(), _c.c_uint64()
+    check(lib().ising_check_counters(_c.byref(c), _c.byref(n), _c.byref(f)), "ising_check_counters")
+    return bool(c.value), n.value, f.value
+
 
 def gauss_legendre(n, a, b):
     x = np.zeros(n)

@@ -505,6 +505,18 @@ int ising_set_sweep(ising* h, uint64_t sweep) {
   return sync_desc(h);
 }
 
+int ising_check_counters(int* checked, uint64_t* count, uint64_t* first) {
+  clear_error();
+  if (!checked || !count || !first) return fail(ISING_EINVAL, "NULL argument");
+  unsigned long long c = 0, f = 0;
+  const int r = read_oob_counters(&c, &f);
+  if (r < 0) return fail(ISING_ECUDA, "cannot read the check counters");
+  *checked = r;
+  *count = c;
+  *first = f;
+  return ISING_OK;
+}
+
 int ising_reserve_records(ising* h, uint64_t n_records) {
   clear_error();
   if (!h) return fail(ISING_EINVAL, "NULL handle");

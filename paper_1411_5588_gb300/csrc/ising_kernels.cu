@@ -30,6 +30,29 @@ namespace {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Checked builds (-DISING_CHECKED) test every lattice word index against its
+// plane before the access: an index out of range is counted, the first one
+// is kept (site << 48 | index), and the access goes to word 0 instead (a
+// store is dropped).  Normal builds compile the checks away.
+#ifdef ISING_CHECKED
+__device__ unsigned long long g_oob_count;
+__device__ unsigned long long g_oob_first;
+__device__ __forceinline__ bool oob(uint64_t idx, uint64_t lim, uint32_t site) {
+  if (idx < lim) return false;
+  atomicAdd(&g_oob_count, 1ull);
+  atomicCAS(&g_oob_first, 0ull, ((unsigned long long)site << 48) | (idx & 0xFFFFFFFFFFFFull));
+  return true;
+}
+#define ISG_LD(p, idx, lim, site) ((p)[oob((idx), (lim), (site)) ? 0 : (idx)])
+#define ISG_ST(p, idx, lim, site, v) \
+  do {                               \
+    if (!oob((idx), (lim), (site))) (p)[(idx)] = (v); \
+  } while (0)
+#else
+#define ISG_LD(p, idx, lim, site) ((p)[(idx)])
+#define ISG_ST(p, idx, lim, site, v) ((p)[(idx)] = (v))
+#endif
+
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
   return (a & b) | (c & (a ^ b));
 }
@@ -82,6 +105,7 @@ struct FilmCtx {
   uint32_t* plane0;
   uint32_t* plane1;
   uint32_t Lx, Ly, n, W, Wp, y_mode, x_pbc, last_mask, last_calls;
+  uint32_t plane_words;  // words of one plane (Lx * Ly * Wp), for checked builds
   const uint32_t* rk0;  // Philox round keys (constant bank or shared memory)
   const uint32_t* rk1;
   uint32_t colour, sweep;
@@ -106,15 +130,20 @@ __device__ __forceinline__ void fetch_word(const FilmCtx& c, uint32_t kx, uint32
   const uint32_t LyWp = Ly * Wp;
   const uint32_t gkx = (c.y_mode == kYGapbc) ? (Lx - kx) : (kx - 1);  // 0-based layer of the wrap row
   f.kx = kx; f.ky = ky; f.w = w;
-  f.S = P[base];
-  f.xm = (kx > 1) ? P[base - LyWp] : (c.x_pbc ? P[base + (Lx - 1) * LyWp] : 0u);
-  f.xp = (kx < Lx) ? P[base + LyWp] : (c.x_pbc ? P[base - (Lx - 1) * LyWp] : 0u);
-  f.ym = (ky > 1) ? P[base - Wp] : P[(gkx * Ly + (Ly - 1)) * Wp + w];
-  f.yp = (ky < Ly) ? P[base + Wp] : P[gkx * LyWp + w];
-  f.z0 = Q[base];
-  if (X == 0) f.za = (w > 0) ? Q[base - 1] : Q[rbase + W - 1];  // previous word, or the row's last
-  else f.za = (w + 1 < W) ? Q[base + 1] : Q[rbase];              // next word, or the row's first
-  f.zf = Q[rbase];
+  const uint32_t lim = c.plane_words;
+  f.S = ISG_LD(P, base, lim, 1);
+  f.xm = (kx > 1) ? ISG_LD(P, base - LyWp, lim, 2)
+                  : (c.x_pbc ? ISG_LD(P, base + (Lx - 1) * LyWp, lim, 3) : 0u);
+  f.xp = (kx < Lx) ? ISG_LD(P, base + LyWp, lim, 4)
+                   : (c.x_pbc ? ISG_LD(P, base - (Lx - 1) * LyWp, lim, 5) : 0u);
+  f.ym = (ky > 1) ? ISG_LD(P, base - Wp, lim, 6) : ISG_LD(P, (gkx * Ly + (Ly - 1)) * Wp + w, lim, 7);
+  f.yp = (ky < Ly) ? ISG_LD(P, base + Wp, lim, 8) : ISG_LD(P, gkx * LyWp + w, lim, 9);
+  f.z0 = ISG_LD(Q, base, lim, 10);
+  if (X == 0)  // previous word, or the row's last
+    f.za = (w > 0) ? ISG_LD(Q, base - 1, lim, 11) : ISG_LD(Q, rbase + W - 1, lim, 12);
+  else  // next word, or the row's first
+    f.za = (w + 1 < W) ? ISG_LD(Q, base + 1, lim, 13) : ISG_LD(Q, rbase, lim, 14);
+  f.zf = ISG_LD(Q, rbase, lim, 15);
 }
 
 // Metropolis decisions for the up to 32 sites of the fetched word; returns
@@ -254,7 +283,7 @@ __device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, u
   const uint32_t row = (f.kx - 1) * c.Ly + (f.ky - 1);
   const uint32_t X = (f.kx + f.ky + 1 + c.colour) & 1u;
   uint32_t* __restrict__ P = X ? c.plane1 : c.plane0;
-  P[row * c.Wp + f.w] = v;
+  ISG_ST(P, row * c.Wp + f.w, c.plane_words, 16, v);
 }
 
 __device__ __forceinline__ void item_word(const FilmCtx& c, uint32_t item, uint32_t dwm, uint32_t dwl,
@@ -387,6 +416,7 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     if (!s_d.active || s_d.sweep + k >= s_d.sweep_end) continue;
     FilmCtx c;
     c.Lx = s_d.Lx; c.Ly = s_d.Ly; c.n = s_d.n; c.W = s_d.W; c.Wp = s_d.Wp;
+    c.plane_words = s_d.Lx * s_d.Ly * s_d.Wp;
     c.y_mode = s_d.y_mode; c.x_pbc = s_d.x_pbc; c.rk0 = s_d.rk0; c.rk1 = s_d.rk1;
     c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
     c.colour = colour; c.sweep = s_d.sweep + k;
@@ -417,6 +447,7 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   pdl_wait();  // the table above needs nothing from the previous grid
   FilmCtx c;
   c.Lx = d.Lx; c.Ly = d.Ly; c.n = d.n; c.W = d.W; c.Wp = d.Wp;
+  c.plane_words = d.Lx * d.Ly * d.Wp;
   c.y_mode = d.y_mode; c.x_pbc = d.x_pbc; c.rk0 = d.rk0; c.rk1 = d.rk1;
   c.last_mask = d.last_mask; c.last_calls = d.last_calls;
   c.colour = colour; c.sweep = sweep;
@@ -457,34 +488,35 @@ __device__ __forceinline__ void measure_word(const uint32_t* A, const uint32_t* 
                                              int& bb) {
   const uint32_t row = kxm1 * Ly + kym1;
   const size_t base = (size_t)row * Wp + w;
+  const size_t lim = (size_t)Lx * Ly * Wp;
   const bool last = (w + 1 == W);
   const uint32_t valid = last ? last_mask : 0xFFFFFFFFu;
   const int nv = __popc(valid);
-  const uint32_t a = A[base], b = B[base];
+  const uint32_t a = ISG_LD(A, base, lim, 21), b = ISG_LD(B, base, lim, 22);
   m = 2 * (__popc(a & valid) + __popc(b & valid)) - 2 * nv;
   bb = 0;
   // +x bond
   if (kxm1 + 1 < Lx) {
     const size_t nb = base + (size_t)Ly * Wp;
-    bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
+    bb += bonds(a, ISG_LD(A, nb, lim, 23), valid, nv) + bonds(b, ISG_LD(B, nb, lim, 24), valid, nv);
   } else if (x_pbc) {
     const size_t nb = base - (size_t)(Lx - 1) * Ly * Wp;
-    bb += bonds(a, A[nb], valid, nv) + bonds(b, B[nb], valid, nv);
+    bb += bonds(a, ISG_LD(A, nb, lim, 25), valid, nv) + bonds(b, ISG_LD(B, nb, lim, 26), valid, nv);
   }
   // +y bond
   if (kym1 + 1 < Ly) {
-    bb += bonds(a, A[base + Wp], valid, nv) + bonds(b, B[base + Wp], valid, nv);
+    bb += bonds(a, ISG_LD(A, base + Wp, lim, 27), valid, nv) + bonds(b, ISG_LD(B, base + Wp, lim, 28), valid, nv);
   } else {
     const uint32_t gkx = (y_mode == kYGapbc) ? (Lx - 1 - kxm1) : kxm1;
     const size_t g = ((size_t)gkx * Ly) * Wp + w;
-    const int y = bonds(a, A[g], valid, nv) + bonds(b, B[g], valid, nv);
+    const int y = bonds(a, ISG_LD(A, g, lim, 29), valid, nv) + bonds(b, ISG_LD(B, g, lim, 30), valid, nv);
     bb += (y_mode != kYPbc) ? -y : y;
   }
   // +z bonds: (2j, 2j+1) inside the word pair, (2j+1, 2j+2) through a shift
   bb += bonds(a, b, valid, nv);
   const size_t rbase = (size_t)row * Wp;
-  uint32_t an = shift_next(a, last ? A[rbase] : A[base + 1]);
-  if (last && last_mask != 0xFFFFFFFFu) an |= (A[rbase] & 1u) << bitpos((n - 1) & 31u);
+  uint32_t an = shift_next(a, last ? ISG_LD(A, rbase, lim, 31) : ISG_LD(A, base + 1, lim, 32));
+  if (last && last_mask != 0xFFFFFFFFu) an |= (ISG_LD(A, rbase, lim, 33) & 1u) << bitpos((n - 1) & 31u);
   bb += bonds(b, an, valid, nv);
 }
 
@@ -666,11 +698,12 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
   for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
     const uint32_t X = i >= words ? 1u : 0u;
     const uint32_t rw = i - X * words, r = rw / W, w = rw - r * W;
-    s_planes[i] = (X ? g1 : g0)[(size_t)r * Wp + w];
+    s_planes[i] = ISG_LD(X ? g1 : g0, (size_t)r * Wp + w, (size_t)Lx * Ly * Wp, 41);
   }
   __syncthreads();
   FilmCtx c;
   c.Lx = Lx; c.Ly = Ly; c.n = s_d.n; c.W = W; c.Wp = W;
+  c.plane_words = words;
   c.y_mode = s_d.y_mode; c.x_pbc = s_d.x_pbc; c.rk0 = s_d.rk0; c.rk1 = s_d.rk1;
   c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
   c.plane0 = s_planes;
@@ -743,7 +776,7 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
   for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
     const uint32_t X = i >= words ? 1u : 0u;
     const uint32_t rw = i - X * words, r = rw / W, w = rw - r * W;
-    (X ? g1 : g0)[(size_t)r * Wp + w] = s_planes[i];
+    ISG_ST(X ? g1 : g0, (size_t)r * Wp + w, (size_t)Lx * Ly * Wp, 42, s_planes[i]);
   }
   if (threadIdx.x == 0) {
     Fg->sweep = s_d.sweep + done;
@@ -918,6 +951,18 @@ cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_byt
     return cudaErrorInvalidValue;
   auto* kern = exact ? resident_kernel<false> : resident_kernel<true>;
   return launch_pdl(kern, n_films, threads, smem_bytes, st, films, pool, records, n_sweeps);
+}
+
+int read_oob_counters(unsigned long long* count, unsigned long long* first) {
+#ifdef ISING_CHECKED
+  if (cudaMemcpyFromSymbol(count, g_oob_count, sizeof *count) != cudaSuccess) return -1;
+  if (cudaMemcpyFromSymbol(first, g_oob_first, sizeof *first) != cudaSuccess) return -1;
+  return 1;
+#else
+  *count = 0;
+  *first = 0;
+  return 0;
+#endif
 }
 
 int update_blocks_per_sm() {

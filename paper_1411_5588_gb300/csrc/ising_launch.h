@@ -81,6 +81,9 @@ uint32_t resident_threads(const FilmDesc& d);
 // the largest.  The kernel advances each descriptor's sweep and rec_next.
 cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_bytes, uint32_t threads, bool exact,
                             uint32_t* pool, int64_t* records, uint32_t n_sweeps, cudaStream_t st);
+// Checked builds: the out-of-range access counters (returns 1); other
+// builds return 0 with both zero; -1 on a CUDA error.
+int read_oob_counters(unsigned long long* count, unsigned long long* first);
 int update_blocks_per_sm();
 int measure_blocks_per_sm();
 
