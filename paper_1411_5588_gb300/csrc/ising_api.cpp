@@ -546,6 +546,7 @@ int ising_autotune(ising* h, uint32_t measure_every, int* shape) {
   const FilmDesc& d = h->d();
   // a scratch film of the same shape and parameters: the kernels do the same
   // work whatever the spins are, and the handle's own chain is not touched
+  DeviceGuard dev(h->fs.device);
   ising* s = nullptr;
   int rc = ising_create(d.Lx, d.Ly, d.Lz, h->J, h->H1, h->T, h->seed, &s);
   if (rc) return rc;

@@ -296,6 +296,7 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   if (!b) return fail(ISING_EINVAL, "NULL batch");
   // a scratch batch of the same films from their initial states: the kernels
   // do the same work whatever the spins are, and this batch is not touched
+  DeviceGuard dev(b->fs.device);
   ising_batch* s = nullptr;
   int rc = ising_batch_create(b->jobs.data(), b->jobs.size(), &s);
   if (rc) return rc;

@@ -93,6 +93,18 @@ inline int items_shape(uint32_t items) {
   return items == 2 ? ISING_SHAPE_GRID_2 : items == 0 ? ISING_SHAPE_GRID_Q : ISING_SHAPE_GRID_1;
 }
 
+// Makes `device` current for the guard's lifetime (the scratch objects of
+// the autotuners live on the tuned object's device).
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess || prev == device || cudaSetDevice(device) != cudaSuccess) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 // Autotuner cache, shared by every handle of the process: the fastest launch
 // shape (ISING_SHAPE_*) measured for a film shape, boundary, table variant
 // and record interval.
