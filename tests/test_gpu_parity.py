@@ -177,6 +177,27 @@ def test_mixed_batch_matches_films_run_alone(cold, shape):
         b.close()
 
 
+def test_records_when_measurement_blocks_outnumber_the_grid():
+    """About 2,000 measurement blocks over 170 films -- layers grouped several
+    to a block, one block per layer, two blocks per layer -- so that the
+    measurement grid strides over films and the block that completes a film
+    (and writes its record) is often serving another film next."""
+    specs = []
+    geoms = [(12, 520, 2)] * 150 + [(5, 1100, 2)] * 10 + [(6, 8, 16)] * 10
+    for i, (Lx, Ly, Lz) in enumerate(geoms):
+        specs.append(dict(Lx=Lx, Ly=Ly, Lz=Lz, T=2.5 + 0.01 * i, H1=0.3, seed=41, replica=i,
+                          measure_every=1 + i % 3, init_kind=ig.INIT_RANDOM, y_mode=[ig.Y_GAPBC, ig.Y_PBC][i % 2]))
+    b = ig.Batch(specs)
+    b.set_shape(ig.SHAPE_GRID_1)
+    b.sweep(12, True)
+    for i, sp in enumerate(specs):
+        o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], y_mode=sp["y_mode"],
+                   replica=sp["replica"])
+        o.init(sp["init_kind"], 0.0)
+        assert np.array_equal(b.read_series(i), o.sweep(12, sp["measure_every"])), i
+    b.close()
+
+
 def test_thermodynamic_integration_from_gpu_records_matches_oracle():
     """The film's own integral over H1 (8 Gauss-Legendre nodes): the FP64 result from the GPU's
     records through the library equals the oracle-fed numpy result to 1e-12."""
