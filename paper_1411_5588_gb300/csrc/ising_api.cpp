@@ -189,13 +189,10 @@ uint32_t FilmSet::fin_grid() const { return std::min<uint32_t>(hh.n_films, (uint
 
 int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_grid) {
   const uint32_t ug = fixed_grid ? upd_grid_max() : upd_grid();
-  const uint32_t mg = fixed_grid ? meas_grid_max() : meas_grid();
   const uint32_t fg = fixed_grid ? (uint32_t)(2 * n_sm) : fin_grid();
   bool exact = false;
   for (const auto& d : h) exact = exact || (d.active && d.has_never);
   for (uint32_t k = k0; k < k0 + n; k++) {
-    ISG_CK(launch_update(L, ug, pool, 0, k, exact, items, stream));
-    ISG_CK(launch_update(L, ug, pool, 1, k, exact, items, stream));
     bool meas = all_meas;
     if (!meas)
       for (const auto& d : h)
@@ -204,7 +201,10 @@ int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_g
           meas = true;
           break;
         }
-    if (meas) ISG_CK(launch_measure(L, mg, fg, pool, part, rec, k + 1, 0, nullptr, stream));
+    // records: half-sweep 1 accumulates the sums, a small kernel writes them
+    ISG_CK(launch_update(L, ug, pool, 0, k, exact, items, nullptr, stream));
+    ISG_CK(launch_update(L, ug, pool, 1, k, exact, items, meas ? part : nullptr, stream));
+    if (meas) ISG_CK(launch_record(L, fg, part, rec, k + 1, stream));
   }
   return ISING_OK;
 }
@@ -352,6 +352,7 @@ int ising_create(int Lx, int Ly, int Lz, double J, double H1, double T, uint64_t
   const size_t words = film_words(d);
   if (cudaMalloc(&h->fs.pool, words * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&h->fs.part, part_len(d) * sizeof(int64_t)) != cudaSuccess ||
+      cudaMemset(h->fs.part, 0, part_len(d) * sizeof(int64_t)) != cudaSuccess ||
       cudaMalloc(&h->d_direct, record_len(d) * sizeof(int64_t)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(h->d_direct);
@@ -626,11 +627,11 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
   const uint32_t items = shape_items(shape);
   for (uint64_t k = 0; k < n; k++) {
     const uint32_t t = (uint32_t)(s0 + k);
-    ISG_CK(launch_update_film(d, h->fs.pool, 0, t, items, h->fs.stream));
-    ISG_CK(launch_update_film(d, h->fs.pool, 1, t, items, h->fs.stream));
-    if (measure_every && (s0 + k + 1) % measure_every == 0)
-      ISG_CK(launch_measure(h->fs.L, h->fs.meas_grid(), 1, h->fs.pool, h->fs.part, h->fs.rec, (uint32_t)(k + 1), 0,
-                            nullptr, h->fs.stream));
+    const bool rec_now = measure_every && (s0 + k + 1) % measure_every == 0;
+    ISG_CK(launch_update_film(d, h->fs.pool, 0, t, items, nullptr, h->fs.stream));
+    ISG_CK(launch_update_film(d, h->fs.pool, 1, t, items, rec_now ? h->fs.part + acc_offset(d) : nullptr,
+                              h->fs.stream));
+    if (rec_now) ISG_CK(launch_record(h->fs.L, 1, h->fs.part, h->fs.rec, (uint32_t)(k + 1), h->fs.stream));
   }
   ISG_CK(launch_advance(h->fs.L, 1, (uint32_t)n, h->fs.stream));
   d.sweep = (uint32_t)(s0 + n);

@@ -162,7 +162,8 @@ int ising_batch_create(const ising_job* jobs, size_t n, ising_batch** out) {
   size_t part = 0;
   for (auto& d : fs.h) part += part_len(d);
   if (cudaMalloc(&fs.pool, words * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc(&fs.part, part * sizeof(int64_t)) != cudaSuccess) {
+      cudaMalloc(&fs.part, part * sizeof(int64_t)) != cudaSuccess ||
+      cudaMemset(fs.part, 0, part * sizeof(int64_t)) != cudaSuccess) {
     cudaGetLastError();
     ising_batch_destroy(b);
     return fail(ISING_ENOMEM, "device allocation of %zu words failed", words);

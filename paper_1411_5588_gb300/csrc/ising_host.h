@@ -38,7 +38,8 @@ void build_tables(FilmDesc& d, double J, double H, double H1, double T);
 // Packed words of one film (both parity planes).
 inline size_t film_words(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.Ly * d.Wp; }
 inline size_t record_len(const FilmDesc& d) { return 5 + (size_t)d.Lx; }
-inline size_t part_len(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.meas_bpl; }
+// Measurement partial sums, then the record accumulators (acc_offset).
+inline size_t part_len(const FilmDesc& d) { return 2 * (size_t)d.Lx * d.meas_bpl + 2 * (size_t)d.Lx; }
 
 // Films updated by the same launches: descriptors, owner tables and the
 // device buffers they point into.

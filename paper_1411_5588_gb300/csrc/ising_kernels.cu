@@ -7,8 +7,12 @@
 //    (kx, 1) -- kx' = Lx+1-kx for the Eq. 11 rule, kx' = kx otherwise.  That
 //    row depends on nothing else updated in the half-sweep, so the thread-local
 //    order reproduces "all of {c, ky<Ly}, then all of {c, ky=Ly}" exactly.
-//  - measure_partial_kernel / measure_finalize_kernel: the int64 sums B, M,
-//    M1, Mn and m(kx) of Eqs. 1, 7, 9, 17 and 19, per-block partials in a
+//    The half-sweep 1 launch of a sweep after which films record also sums
+//    their int64 record quantities B, M, M1, Mn and m(kx) (Eqs. 1, 7, 9, 17,
+//    19) from the words it holds in registers, into per-layer accumulators.
+//  - record_kernel: writes those records and clears the accumulators.
+//  - measure_partial_kernel / measure_finalize_kernel: the same sums from the
+//    lattice alone (an on-demand measurement), per-block partials in a
 //    scratch area, then one block per film writes the record.
 //  - init_kernel, pack_kernel, unpack_kernel, advance_kernel.
 #include <cuda_runtime.h>
@@ -49,8 +53,8 @@ __device__ __forceinline__ bool oob(uint64_t idx, uint64_t lim, uint32_t site) {
     if (!oob((idx), (lim), (site))) (p)[(idx)] = (v); \
   } while (0)
 #else
-#define ISG_LD(p, idx, lim, site) ((p)[(idx)])
-#define ISG_ST(p, idx, lim, site, v) ((p)[(idx)] = (v))
+#define ISG_LD(p, idx, lim, site) ((void)(lim), (p)[(idx)])
+#define ISG_ST(p, idx, lim, site, v) ((void)(lim), (p)[(idx)] = (v))
 #endif
 
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
@@ -106,10 +110,22 @@ struct FilmCtx {
   uint32_t* plane1;
   uint32_t Lx, Ly, n, W, Wp, y_mode, x_pbc, last_mask, last_calls;
   uint32_t plane_words;  // words of one plane (Lx * Ly * Wp), for checked builds
+  uint32_t seam_same;    // the y-wrap bonds join sites of one colour (Lx+Ly even under Eq. 11, Ly odd otherwise)
   const uint32_t* rk0;  // Philox round keys (constant bank or shared memory)
   const uint32_t* rk1;
   uint32_t colour, sweep;
 };
+
+__host__ __device__ inline uint32_t seam_joins_one_colour(uint32_t Lx, uint32_t Ly, uint32_t y_mode) {
+  return y_mode == kYGapbc ? ((Lx + Ly) % 2 == 0) : (Ly % 2 == 1);
+}
+
+// Whether film F records after `done` sweeps of the current chunk.
+__device__ __forceinline__ bool measured_now(const FilmDesc& F, uint32_t done, int force) {
+  if (force) return true;
+  if (F.measure_every == 0 || done == 0 || F.sweep_end - F.sweep < done) return false;
+  return ((F.sweep + done) % F.measure_every) == 0;
+}
 
 // The words one thread needs to update word w of row (kx, ky), loaded ahead
 // of the arithmetic so that the loads of the next word overlap the current
@@ -150,11 +166,26 @@ __device__ __forceinline__ void fetch_word(const FilmCtx& c, uint32_t kx, uint32
 // the mask of sites that flip.  QUARTER: only Philox calls qsel and qsel + 4
 // (the sites at bits qsel and qsel + 4 of each byte), for a word shared by
 // four lanes.
+// The other array's word w shifted by one site onto this word's sites, so
+// that each site meets its second z-neighbour: site j of array 0 meets site
+// j - 1 of array 1, site j of array 1 meets site j + 1 of array 0, and the
+// row's ends meet through the periodic z wrap.
+template <bool FULL>
+__device__ __forceinline__ uint32_t z_shifted(const FilmCtx& c, const Fetched& f, uint32_t X) {
+  if (X == 0) {
+    const uint32_t pw = (f.w > 0) ? f.za : (((f.za >> bitpos((c.n - 1) & 31u)) & 1u) << 31);
+    return shift_prev(f.z0, pw);
+  }
+  uint32_t Zs = shift_next(f.z0, f.za);
+  if (!FULL) Zs |= (f.zf & 1u) << bitpos((c.n - 1) & 31u);
+  return Zs;
+}
+
 template <bool FULL, bool FAST, bool QUARTER>
 __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched& f,
                                                 const uint32_t* __restrict__ s_thr,
                                                 const uint32_t* __restrict__ s_alw, uint32_t qsel) {
-  const uint32_t Lx = c.Lx, Ly = c.Ly, W = c.W;
+  const uint32_t Lx = c.Lx, Ly = c.Ly;
   const uint32_t kx = f.kx, ky = f.ky, w = f.w;
   const uint32_t row = (kx - 1) * Ly + (ky - 1);
   const uint32_t X = (kx + ky + 1 + c.colour) & 1u;
@@ -168,14 +199,7 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const uint32_t a1 = ~(S ^ f.xp) & xp_on;
   const uint32_t a2 = ~(S ^ f.ym ^ (ky > 1 ? 0u : negm));
   const uint32_t a3 = ~(S ^ f.yp ^ (ky < Ly ? 0u : negm));
-  uint32_t Zs;
-  if (X == 0) {
-    const uint32_t pw = (w > 0) ? f.za : (((f.za >> bitpos((c.n - 1) & 31u)) & 1u) << 31);
-    Zs = shift_prev(f.z0, pw);
-  } else {
-    Zs = shift_next(f.z0, f.za);
-    if (!FULL) Zs |= (f.zf & 1u) << bitpos((c.n - 1) & 31u);
-  }
+  const uint32_t Zs = z_shifted<FULL>(c, f, X);
   const uint32_t a4 = ~(S ^ f.z0);
   const uint32_t a5 = ~(S ^ Zs);
 
@@ -279,6 +303,70 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   return (lt | alw) & valid;
 }
 
+// Record sums of one word after its update to v (row (f.kx, f.ky), this
+// half-sweep's array X): the magnetisation of the row's two words w, and the
+// sum of sigma_b S_i S_j over the bonds from the word's sites to their six
+// neighbours (an empty x slot is no bond).  In half-sweep 1 every neighbour
+// word is final here -- it holds the other colour, or it is the wrap partner
+// this thread updated just before -- except the -y word of a ky = 1 row when
+// the seam joins one colour (its partner is updated after it); skip_ym
+// leaves that bond to the partner, which counts it from its +y side.
+struct LayerSums {
+  uint32_t layer = 0xFFFFFFFFu;  // 0-based kx, none when 0xFFFFFFFF
+  int m = 0, b = 0;
+};
+
+__device__ __forceinline__ LayerSums word_sums(const FilmCtx& c, const Fetched& f, uint32_t v, bool skip_ym) {
+  const uint32_t X = (f.kx + f.ky + 1 + c.colour) & 1u;
+  const bool last = f.w + 1 == c.W;
+  const uint32_t valid = last ? c.last_mask : 0xFFFFFFFFu;
+  const int nv = __popc(valid);
+  const uint32_t negm = (c.y_mode != kYPbc) ? 0xFFFFFFFFu : 0u;
+  const uint32_t Zs = (last && c.last_mask != 0xFFFFFFFFu) ? z_shifted<false>(c, f, X) : z_shifted<true>(c, f, X);
+  int pa = __popc(~(v ^ f.yp ^ (f.ky < c.Ly ? 0u : negm)) & valid) + __popc(~(v ^ f.z0) & valid) +
+           __popc(~(v ^ Zs) & valid);
+  int nd = 3;
+  if (f.kx > 1 || c.x_pbc) { pa += __popc(~(v ^ f.xm) & valid); nd++; }
+  if (f.kx < c.Lx || c.x_pbc) { pa += __popc(~(v ^ f.xp) & valid); nd++; }
+  if (!skip_ym) { pa += __popc(~(v ^ f.ym ^ (f.ky > 1 ? 0u : negm)) & valid); nd++; }
+  LayerSums r;
+  r.layer = f.kx - 1;
+  r.m = 2 * (__popc(v & valid) + __popc(f.z0 & valid)) - 2 * nv;
+  r.b = 2 * pa - nd * nv;
+  return r;
+}
+
+// The seam bonds between the other arrays of a ky = 1 row (its word f) and
+// its partner row (word g) when the seam joins one colour: neither end is
+// updated in half-sweep 1, so the thread that holds both counts them.
+__device__ __forceinline__ int seam_other_bonds(const FilmCtx& c, const Fetched& f, const Fetched& g) {
+  const uint32_t valid = (f.w + 1 == c.W) ? c.last_mask : 0xFFFFFFFFu;
+  const int s = __popc(valid) - 2 * __popc((f.z0 ^ g.z0) & valid);
+  return c.y_mode != kYPbc ? -s : s;
+}
+
+// Adds the sums of every lane that has some into the film's per-layer int64
+// accumulators [2 kx (magnetisation), 2 kx + 1 (bonds)].  All 32 lanes call
+// it.  A warp whose sums all fall in one layer adds them with two atomics,
+// otherwise each lane adds its own.  Integer atomics: exact in any order.
+__device__ __forceinline__ void add_layer_sums(unsigned long long* acc, const LayerSums& r) {
+  const bool on = r.layer != 0xFFFFFFFFu;
+  const uint32_t act = __ballot_sync(0xFFFFFFFFu, on);
+  if (act == 0) return;
+  const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, r.layer, __ffs(act) - 1);
+  if (__all_sync(0xFFFFFFFFu, !on || r.layer == l0)) {
+    const int m = __reduce_add_sync(0xFFFFFFFFu, on ? r.m : 0);
+    const int b = __reduce_add_sync(0xFFFFFFFFu, on ? r.b : 0);
+    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(act) - 1)) {
+      atomicAdd(acc + 2 * (size_t)l0, (unsigned long long)(long long)m);
+      atomicAdd(acc + 2 * (size_t)l0 + 1, (unsigned long long)(long long)b);
+    }
+  } else if (on) {
+    atomicAdd(acc + 2 * (size_t)r.layer, (unsigned long long)(long long)r.m);
+    atomicAdd(acc + 2 * (size_t)r.layer + 1, (unsigned long long)(long long)r.b);
+  }
+}
+
 __device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, uint32_t v) {
   const uint32_t row = (f.kx - 1) * c.Ly + (f.ky - 1);
   const uint32_t X = (f.kx + f.ky + 1 + c.colour) & 1u;
@@ -295,13 +383,17 @@ __device__ __forceinline__ void item_word(const FilmCtx& c, uint32_t item, uint3
   kx = kxm1 + 1;
 }
 
-template <bool FAST>
+// MEAS: also return the record sums of the word (r1) and of its partner word
+// (r2, ky = 1 only); see word_sums.
+template <bool FAST, bool MEAS = false>
 __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
-                                               const uint32_t* s_alw) {
+                                               const uint32_t* s_alw, LayerSums* r1 = nullptr,
+                                               LayerSums* r2 = nullptr) {
   const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
   const uint32_t v = f.S ^ (full ? decide_word<true, FAST, false>(c, f, s_thr, s_alw, 0)
                                  : decide_word<false, FAST, false>(c, f, s_thr, s_alw, 0));
   store_word(c, f, v);
+  if (MEAS) *r1 = word_sums(c, f, v, f.ky == 1 && c.seam_same);
   // ky = 1 rows then update their wrap partner row (kx', Ly); its wrap
   // neighbour is the word just written, so it is fetched only now
   if (f.ky == 1) {
@@ -311,16 +403,20 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
     const uint32_t v2 = g.S ^ (full ? decide_word<true, FAST, false>(c, g, s_thr, s_alw, 0)
                                     : decide_word<false, FAST, false>(c, g, s_thr, s_alw, 0));
     store_word(c, g, v2);
+    if (MEAS) {
+      *r2 = word_sums(c, g, v2, false);
+      if (c.seam_same) r2->b += seam_other_bonds(c, f, g);
+    }
   }
 }
 
 // The same for a word shared by the four lanes 4j..4j+3 of a warp (lane qsel
 // draws Philox calls qsel and qsel + 4); gmask holds the lanes whose group has
 // a word.  The lanes merge their flip masks and the group's lane 0 stores.
-template <bool FAST>
+template <bool FAST, bool MEAS>
 __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const Fetched& f, bool on, uint32_t qsel,
                                                        uint32_t gmask, const uint32_t* s_thr,
-                                                       const uint32_t* s_alw) {
+                                                       const uint32_t* s_alw, LayerSums& r1, LayerSums& r2) {
   const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
   uint32_t fl = 0;
   if (on) fl = full ? decide_word<true, FAST, true>(c, f, s_thr, s_alw, qsel)
@@ -329,6 +425,7 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
   fl |= __shfl_xor_sync(gmask, fl, 1);
   fl |= __shfl_xor_sync(gmask, fl, 2);
   if (qsel == 0) store_word(c, f, f.S ^ fl);
+  if (MEAS && qsel == 0) r1 = word_sums(c, f, f.S ^ fl, f.ky == 1 && c.seam_same);
   // ky = 1 words then update their wrap partner word (see update_fetched)
   const uint32_t pmask = __ballot_sync(gmask, f.ky == 1);
   if (f.ky != 1) return;
@@ -341,17 +438,24 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
   fl2 |= __shfl_xor_sync(pmask, fl2, 1);
   fl2 |= __shfl_xor_sync(pmask, fl2, 2);
   if (qsel == 0) store_word(c, g, g.S ^ fl2);
+  if (MEAS && qsel == 0) {
+    r2 = word_sums(c, g, g.S ^ fl2, false);
+    if (c.seam_same) r2.b += seam_other_bonds(c, f, g);
+  }
 }
 
 }  // namespace
 
 // The words of one block of words_per_block(ITEMS) consecutive words: each
 // thread fetches its ITEMS words (kFilmThreads apart) before deciding any;
-// ITEMS = 0: four lanes per word (kFilmThreads / 4 words).
-template <bool FAST, uint32_t ITEMS>
+// ITEMS = 0: four lanes per word (kFilmThreads / 4 words).  MEAS and acc set
+// (half-sweep 1 of a sweep after which the film records): the words' record
+// sums go into the film's per-layer accumulators acc.
+template <bool FAST, uint32_t ITEMS, bool MEAS>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
-                                            const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw) {
+                                            const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw,
+                                            unsigned long long* acc) {
   if (ITEMS == 0) {
     const uint32_t item = first + (threadIdx.x >> 2);
     const bool on = item < items;
@@ -362,7 +466,14 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
       item_word(c, item, dwm, dwl, dym, dyl, kx, ky, w);
       fetch_word(c, kx, ky, w, f);
     }
-    update_fetched_quarter<FAST>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw);
+    LayerSums r1, r2;
+    if (MEAS && acc) {
+      update_fetched_quarter<FAST, true>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, r1, r2);
+      add_layer_sums(acc, r1);
+      add_layer_sums(acc, r2);
+    } else {
+      update_fetched_quarter<FAST, false>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, r1, r2);
+    }
     return;
   }
   constexpr uint32_t NI = ITEMS == 0 ? 1 : ITEMS;
@@ -378,6 +489,16 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
       fetch_word(c, kx, ky, w, fw[it]);
     }
   }
+  if (MEAS && acc) {
+#pragma unroll
+    for (uint32_t it = 0; it < NI; it++) {
+      LayerSums r1, r2;
+      if (mine[it]) update_fetched<FAST, true>(c, fw[it], s_thr, s_alw, &r1, &r2);
+      add_layer_sums(acc, r1);
+      add_layer_sums(acc, r2);
+    }
+    return;
+  }
 #pragma unroll
   for (uint32_t it = 0; it < NI; it++)
     if (mine[it]) update_fetched<FAST>(c, fw[it], s_thr, s_alw);
@@ -387,11 +508,14 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // words of film owner[b], whose descriptor is staged in shared memory.  FAST:
 // no film of the launch has a reachable thr = 0 entry (the compare-only
 // table); otherwise every film takes the exact variant (which, at two words
-// per thread, needs the registers of one block per SM fewer).
-template <bool FAST, uint32_t ITEMS>
-__global__ void __launch_bounds__(kFilmThreads, (FAST || ITEMS < 2) ? kMultiMinBlocks : kMultiMinBlocks - 1)
+// per thread, needs the registers of one block per SM fewer).  MEAS: the
+// half-sweep 1 launch of a sweep after which some film records; those films
+// add their record sums into their accumulators in `part`.
+template <bool FAST, uint32_t ITEMS, bool MEAS>
+__global__ void __launch_bounds__(kFilmThreads, ((FAST || ITEMS < 2) && !MEAS) ? kMultiMinBlocks : kMultiMinBlocks - 1)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
-              const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k) {
+              const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k,
+              int64_t* __restrict__ part) {
   constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
   static_assert(sizeof(FilmDesc) % 16 == 0, "descriptor copied as uint4");
   __shared__ __align__(16) FilmDesc s_d;
@@ -422,19 +546,25 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     c.colour = colour; c.sweep = s_d.sweep + k;
     c.plane0 = pool + s_d.spin_off;
     c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
+    c.seam_same = seam_joins_one_colour(c.Lx, c.Ly, c.y_mode);
+    unsigned long long* acc = nullptr;
+    if (MEAS && colour == 1 && measured_now(s_d, k + 1, 0))
+      acc = reinterpret_cast<unsigned long long*>(part + acc_offset(s_d));
     const uint32_t first = (vb - s_d.upd_block_begin) * words_per_block(ITEMS);
-    sweep_block<FAST, ITEMS>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo, s_alw);
+    sweep_block<FAST, ITEMS, MEAS>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
+                                   s_alw, acc);
   }
 }
 
 // Single-film half-sweep.  The descriptor is a __grid_constant__ kernel
 // parameter, so every per-film constant (round keys included) is read straight
 // from the constant bank; block b updates words b * words_per_block(ITEMS)
-// onwards.
-template <bool FAST, uint32_t ITEMS>
-__global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
+// onwards.  MEAS: half-sweep 1 before a record, whose sums go into the
+// film's accumulators acc.
+template <bool FAST, uint32_t ITEMS, bool MEAS>
+__global__ void __launch_bounds__(kFilmThreads, MEAS ? kFilmMinBlocks - 1 : kFilmMinBlocks)
 update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
-                   uint32_t sweep) {
+                   uint32_t sweep, int64_t* __restrict__ acc) {
   pdl_trigger();
   __shared__ __align__(16) uint32_t s_thr[64];
   __shared__ __align__(16) uint32_t s_alw[64];
@@ -453,8 +583,9 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   c.colour = colour; c.sweep = sweep;
   c.plane0 = pool + d.spin_off;
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
-  sweep_block<FAST, ITEMS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m, d.divy_l, s_thr,
-                    s_alw);
+  c.seam_same = seam_joins_one_colour(d.Lx, d.Ly, d.y_mode);
+  sweep_block<FAST, ITEMS, MEAS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
+                                 d.divy_l, s_thr, s_alw, MEAS ? reinterpret_cast<unsigned long long*>(acc) : nullptr);
 }
 
 // ------------------------------------------------------------ measurement
@@ -518,12 +649,6 @@ __device__ __forceinline__ void measure_word(const uint32_t* A, const uint32_t* 
   uint32_t an = shift_next(a, last ? ISG_LD(A, rbase, lim, 31) : ISG_LD(A, base + 1, lim, 32));
   if (last && last_mask != 0xFFFFFFFFu) an |= (ISG_LD(A, rbase, lim, 33) & 1u) << bitpos((n - 1) & 31u);
   bb += bonds(b, an, valid, nv);
-}
-
-__device__ __forceinline__ bool measured_now(const FilmDesc& F, uint32_t done, int force) {
-  if (force) return true;
-  if (F.measure_every == 0 || done == 0 || F.sweep_end - F.sweep < done) return false;
-  return ((F.sweep + done) % F.measure_every) == 0;
 }
 
 }  // namespace
@@ -648,6 +773,48 @@ measure_finalize_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restric
   }
 }
 
+// Records of the films that record after `done` sweeps of the chunk, from
+// the per-layer sums half-sweep 1 accumulated; the accumulators are cleared
+// for the next record.
+__global__ void __launch_bounds__(kMeasureBlock)
+record_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restrict__ hdr, int64_t* __restrict__ part,
+              int64_t* __restrict__ records, uint32_t done) {
+  __shared__ int64_t s_red[kMeasureBlock / 32];
+  __shared__ uint32_t s_slot;
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t nf = hdr->n_films;
+  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
+    FilmDesc& F = films[f];
+    if (!F.active || !measured_now(F, done, 0)) continue;
+    const uint32_t Lx = F.Lx;
+    __syncthreads();
+    if (threadIdx.x == 0) s_slot = F.rec_cap ? (F.rec_next % F.rec_cap) : 0u;
+    __syncthreads();
+    int64_t* rec = records + F.rec_off + (size_t)s_slot * (5 + Lx);
+    int64_t* acc = part + acc_offset(F);
+    int64_t M = 0, Bs = 0;
+    for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) {
+      const int64_t m = acc[2 * kx], b = acc[2 * kx + 1];
+      acc[2 * kx] = 0;
+      acc[2 * kx + 1] = 0;
+      rec[5 + kx] = m;
+      M += m;
+      Bs += b;
+    }
+    const int64_t tM = block_sum(M, s_red);
+    const int64_t tB = block_sum(Bs, s_red);
+    if (threadIdx.x == 0) {
+      rec[0] = (int64_t)F.sweep + done;
+      rec[1] = tB;
+      rec[2] = tM;
+      rec[3] = rec[5];
+      rec[4] = rec[5 + Lx - 1];
+      F.rec_next = F.rec_next + 1;
+    }
+  }
+}
+
 __global__ void advance_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restrict__ hdr, uint32_t n_sweeps) {
   pdl_trigger();
   pdl_wait();
@@ -708,6 +875,7 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
   c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
   c.plane0 = s_planes;
   c.plane1 = s_planes + words;
+  c.seam_same = seam_joins_one_colour(Lx, Ly, s_d.y_mode);
   const uint32_t items = s_d.upd_items;
   const uint32_t m_every = s_d.measure_every;
   uint32_t rec_next = s_d.rec_next;
@@ -875,26 +1043,49 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, 
 
 }  // namespace
 
+namespace {
+
+template <bool MEAS>
+auto update_variant(bool exact, uint32_t items) {
+  return exact ? (items == 2 ? update_kernel<false, 2, MEAS>
+                             : items == 1 ? update_kernel<false, 1, MEAS> : update_kernel<false, 0, MEAS>)
+               : (items == 2 ? update_kernel<true, 2, MEAS>
+                             : items == 1 ? update_kernel<true, 1, MEAS> : update_kernel<true, 0, MEAS>);
+}
+
+template <bool MEAS>
+auto update_film_variant(bool exact, uint32_t items) {
+  return exact ? (items == 2 ? update_film_kernel<false, 2, MEAS>
+                             : items == 1 ? update_film_kernel<false, 1, MEAS> : update_film_kernel<false, 0, MEAS>)
+               : (items == 2 ? update_film_kernel<true, 2, MEAS>
+                             : items == 1 ? update_film_kernel<true, 1, MEAS> : update_film_kernel<true, 0, MEAS>);
+}
+
+}  // namespace
+
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          uint32_t items, cudaStream_t st) {
+                          uint32_t items, int64_t* part, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  auto* kern = exact ? (items == 2 ? update_kernel<false, 2> : items == 1 ? update_kernel<false, 1> : update_kernel<false, 0>)
-                     : (items == 2 ? update_kernel<true, 2> : items == 1 ? update_kernel<true, 1> : update_kernel<true, 0>);
+  auto* kern = part ? update_variant<true>(exact, items) : update_variant<false>(exact, items);
   return launch_pdl(kern, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
-                    (const LaunchHdr*)L.hdr, pool, colour, k);
+                    (const LaunchHdr*)L.hdr, pool, colour, k, part);
 }
 
 cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep, uint32_t items,
-                               cudaStream_t st) {
+                               int64_t* acc, cudaStream_t st) {
   const uint32_t ipb = words_per_block(items);
   const uint32_t grid = (d.upd_items + ipb - 1) / ipb;
   if (grid == 0) return cudaSuccess;
-  auto* kern = d.has_never
-                   ? (items == 2 ? update_film_kernel<false, 2> : items == 1 ? update_film_kernel<false, 1>
-                                                                             : update_film_kernel<false, 0>)
-                   : (items == 2 ? update_film_kernel<true, 2> : items == 1 ? update_film_kernel<true, 1>
-                                                                            : update_film_kernel<true, 0>);
-  return launch_pdl(kern, grid, kFilmThreads, 0, st, d, pool, colour, sweep);
+  const bool exact = d.has_never != 0;
+  auto* kern = acc ? update_film_variant<true>(exact, items) : update_film_variant<false>(exact, items);
+  return launch_pdl(kern, grid, kFilmThreads, 0, st, d, pool, colour, sweep, acc);
+}
+
+cudaError_t launch_record(const LaunchSet& L, uint32_t grid, int64_t* part, int64_t* records, uint32_t done,
+                          cudaStream_t st) {
+  if (grid == 0) return cudaSuccess;
+  return launch_pdl(record_kernel, grid, kMeasureBlock, 0, st, L.films, (const LaunchHdr*)L.hdr, part, records,
+                    done);
 }
 
 cudaError_t launch_measure(const LaunchSet& L, uint32_t grid, uint32_t fin_grid, const uint32_t* pool,
@@ -967,7 +1158,7 @@ int read_oob_counters(unsigned long long* count, unsigned long long* first) {
 
 int update_blocks_per_sm() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<true, 1>, kFilmThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<true, 1, false>, kFilmThreads, 0) != cudaSuccess)
     return 0;
   return nb;
 }

@@ -30,6 +30,12 @@ constexpr int kMeasureBlock = 256;
 constexpr uint32_t kMeasureItemsPerBlock = 4 * kMeasureBlock;
 constexpr uint32_t kMeasureMaxLpu = 64;
 
+// The film's per-layer record accumulators (int64 pairs: magnetisation,
+// bonds; Lx of them) follow its measurement partial sums in the same area.
+__host__ __device__ inline uint64_t acc_offset(const FilmDesc& d) {
+  return d.part_off + 2ull * d.Lx * d.meas_bpl;
+}
+
 // Measurement blocks of one film.
 inline uint32_t meas_units(const FilmDesc& d) {
   return d.meas_lpu > 1 ? (d.Lx + d.meas_lpu - 1) / d.meas_lpu : d.Lx * d.meas_bpl;
@@ -57,13 +63,20 @@ struct LaunchSet {
 
 // exact: some film of the launch has a reachable thr = 0 entry (has_never);
 // items: words per thread (1 or 2, or 0 for four lanes per word), matching the
-// owner table's block size.
+// owner table's block size.  part (colour 1 only, else null): the films that
+// record after sweep k add their record sums into their accumulators there;
+// launch_record then writes the records.
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          uint32_t items, cudaStream_t st);
+                          uint32_t items, int64_t* part, cudaStream_t st);
 // One half-sweep of a single film whose descriptor (with `sweep` absolute) is
-// passed by value.
+// passed by value; acc (colour 1 of a recorded sweep, else null): the film's
+// accumulators.
 cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep, uint32_t items,
-                               cudaStream_t st);
+                               int64_t* acc, cudaStream_t st);
+// Records of the films that record after `done` sweeps of the chunk, from the
+// accumulators the half-sweep 1 launch filled (which it clears).
+cudaError_t launch_record(const LaunchSet& L, uint32_t grid, int64_t* part, int64_t* records, uint32_t done,
+                          cudaStream_t st);
 cudaError_t launch_measure(const LaunchSet& L, uint32_t grid, uint32_t fin_grid, const uint32_t* pool,
                            int64_t* part, int64_t* records, uint32_t done, int force, int64_t* direct,
                            cudaStream_t st);

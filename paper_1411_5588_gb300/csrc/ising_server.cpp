@@ -335,6 +335,11 @@ void ising_server::loop() {
     }
     for (Job* j : fresh) {
       if (rc) break;
+      // the record accumulators start at zero (the area may hold an earlier job's data)
+      if (cudaMemsetAsync(arena_dev + j->off_part, 0, j->b_part, fs.stream) != cudaSuccess) {
+        rc = fail(ISING_ECUDA, "partial-sum clear failed");
+        break;
+      }
       uint32_t flip_lo = 0;
       int flip_all = 0;
       if (j->p.init_kind == ISING_INIT_SLAB_Y) {

@@ -1,8 +1,10 @@
-"""Run the 64-film integration set (16 H1 nodes x 2 T x 2 seeds, Lx 32..96)
-as one batch for a few sweeps in a given launch shape; the command the
-multi-film update kernel's ncu summary in profiles/ was captured from.
+"""Run one film set as a batch for a few sweeps in a given launch shape: the
+64-film integration set (16 H1 nodes x 2 T x 2 seeds, Lx 32..96) or one of
+the procedure sets at the paper's sizes (contact angle, beta integration,
+line tension), records after every sweep.  The command the batch kernels'
+ncu summaries in profiles/ were captured from.
 
-    python -m paper_1411_5588_gb300.profile_batch [--shape grid2] [--sweeps 4]
+    python -m paper_1411_5588_gb300.profile_batch [--set ti64] [--shape grid2] [--sweeps 4]
 """
 from __future__ import annotations
 
@@ -12,20 +14,28 @@ from . import binding as ig
 from . import workloads as WL
 
 SHAPES = {"grid1": ig.SHAPE_GRID_1, "grid2": ig.SHAPE_GRID_2, "gridq": ig.SHAPE_GRID_Q}
+SETS = {
+    "ti64": lambda n: WL.ti_batch(n_sweeps=n),
+    "contact_angle": lambda n: WL.contact_angle_set(n_sweeps=n)["jobs"],
+    "interface_tension": lambda n: WL.interface_tension_set(n_sweeps=n)["jobs"],
+    "line_tension": lambda n: WL.line_tension_set(n_sweeps=n)["jobs"],
+}
 
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--set", default="ti64", choices=sorted(SETS))
     ap.add_argument("--shape", default="grid2", choices=sorted(SHAPES))
     ap.add_argument("--sweeps", type=int, default=4)
     args = ap.parse_args()
-    jobs = WL.ti_batch(n_sweeps=args.sweeps)
+    jobs = SETS[args.set](args.sweeps)
     b = ig.Batch(jobs)
     b.set_shape(SHAPES[args.shape])
+    b.reserve_records(args.sweeps)
     b.sweep(args.sweeps, False)
     b.synchronize()
     b.close()
-    print(f"{len(jobs)} films, {args.sweeps} sweeps, shape {args.shape}")
+    print(f"{args.set}: {len(jobs)} films, {args.sweeps} sweeps, shape {args.shape}")
 
 
 if __name__ == "__main__":
