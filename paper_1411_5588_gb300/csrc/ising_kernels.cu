@@ -166,6 +166,100 @@ __device__ __forceinline__ void fetch_word(const FilmCtx& c, uint32_t kx, uint32
 // the mask of sites that flip.  QUARTER: only Philox calls qsel and qsel + 4
 // (the sites at bits qsel and qsel + 4 of each byte), for a word shared by
 // four lanes.
+// Record sums of half-sweep 1.  After its update every neighbour word a
+// thread loaded is final -- it holds the other colour -- except the -y word
+// of a ky = 1 row when the seam joins one colour: that is its wrap partner,
+// which the same thread updates right after it.  So each thread can add up,
+// for its word, the magnetisation of the row's two words w and
+// sum sigma_b S_i S_j over the bonds from the word's sites to their
+// neighbours (an empty x slot is no bond), and every bond of the film is
+// counted once; the seam cases are settled in the partner step.
+//
+// The bonds come from the bit-sliced aligned-neighbour count (c0, c1, c2) of
+// the decision: a flip toggles every aligned mask of its site, so over the
+// D bond slots of the word
+//   sum_d popc(a'_d) = n_old + D popc(fl) - 2 n_fl,
+// n_old and n_fl being the aligned counts summed over the valid and over the
+// flipped sites.  decide_word parks c0, c1, c2 and the row's other word z0 in
+// the thread's shared-memory slots (stride kFilmThreads) across the Philox
+// draws, so the sums cost no registers there.
+constexpr uint32_t kStashSlots = 5;
+
+struct LayerSums {
+  uint32_t layer = 0xFFFFFFFFu;  // 0-based kx, none when 0xFFFFFFFF
+  int m = 0, b = 0;
+};
+
+__device__ __forceinline__ void stash_counts(uint32_t* stash, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t z0) {
+  stash[0] = c0;
+  stash[kFilmThreads] = c1;
+  stash[2 * kFilmThreads] = c2;
+  stash[3 * kFilmThreads] = z0;
+}
+
+// Sums of the word of layer kx (1-based) whose flips were fl and whose new
+// value is v, from the counts decide_word parked.
+__device__ __forceinline__ LayerSums word_sums(const FilmCtx& c, uint32_t kx, uint32_t w, uint32_t fl, uint32_t v,
+                                               const uint32_t* stash) {
+  const uint32_t valid = (w + 1 == c.W) ? c.last_mask : 0xFFFFFFFFu;
+  const int nv = __popc(valid);
+  const uint32_t c0 = stash[0], c1 = stash[kFilmThreads], c2 = stash[2 * kFilmThreads];
+  const uint32_t z0 = stash[3 * kFilmThreads];
+  const int D = 4 + ((kx > 1 || c.x_pbc) ? 1 : 0) + ((kx < c.Lx || c.x_pbc) ? 1 : 0);
+  const int n_old = __popc(c0 & valid) + 2 * __popc(c1 & valid) + 4 * __popc(c2 & valid);
+  const int n_fl = __popc(c0 & fl) + 2 * __popc(c1 & fl) + 4 * __popc(c2 & fl);
+  LayerSums r;
+  r.layer = kx - 1;
+  r.b = 2 * (n_old + D * __popc(fl) - 2 * n_fl) - D * nv;
+  r.m = 2 * (__popc(v & valid) + __popc(z0 & valid)) - 2 * nv;
+  return r;
+}
+
+// Seam correction of a ky = 1 word (new value v, other word z0f) and its
+// partner word g (just fetched) when the seam joins one colour: the word's
+// -y count used the partner's old word, so it comes out again (the partner
+// counts that bond from its +y side with both final words), and the seam
+// bonds between the two rows' other arrays, which no one else holds, go in.
+__device__ __forceinline__ int seam_adjust(const FilmCtx& c, uint32_t w, uint32_t v, uint32_t z0f,
+                                           const Fetched& g) {
+  const uint32_t valid = (w + 1 == c.W) ? c.last_mask : 0xFFFFFFFFu;
+  const int nv = __popc(valid);
+  const bool neg = c.y_mode != kYPbc;
+  const int stale = 2 * __popc(~(v ^ g.S ^ (neg ? 0xFFFFFFFFu : 0u)) & valid) - nv;
+  const int other = nv - 2 * __popc((z0f ^ g.z0) & valid);
+  return (neg ? -other : other) - stale;
+}
+
+// Adds the sums of every lane that has some into the film's per-layer int64
+// accumulators [2 kx (magnetisation), 2 kx + 1 (bonds)].  All 32 lanes call
+// it.  The lanes in the first active lane's layer add with two warp
+// reductions and two atomics; any other lane adds its own.  Integer atomics
+// are exact in any order.
+__device__ __forceinline__ void add_layer_sums(unsigned long long* acc, const LayerSums& r) {
+  const bool on = r.layer != 0xFFFFFFFFu;
+  const uint32_t act = __ballot_sync(0xFFFFFFFFu, on);
+  if (act == 0) return;
+  const int lead = __ffs(act) - 1;
+  const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, r.layer, lead);
+  const bool in0 = on && r.layer == l0;
+  const int m = __reduce_add_sync(0xFFFFFFFFu, in0 ? r.m : 0);
+  const int b = __reduce_add_sync(0xFFFFFFFFu, in0 ? r.b : 0);
+  if ((int)(threadIdx.x & 31u) == lead) {
+    atomicAdd(acc + 2 * (size_t)l0, (unsigned long long)(long long)m);
+    atomicAdd(acc + 2 * (size_t)l0 + 1, (unsigned long long)(long long)b);
+  } else if (on && !in0) {
+    atomicAdd(acc + 2 * (size_t)r.layer, (unsigned long long)(long long)r.m);
+    atomicAdd(acc + 2 * (size_t)r.layer + 1, (unsigned long long)(long long)r.b);
+  }
+}
+
+// A lane's own sums, without a warp reduction (partner words: a few lanes).
+__device__ __forceinline__ void add_lane_sums(unsigned long long* acc, const LayerSums& r) {
+  if (r.layer == 0xFFFFFFFFu) return;
+  atomicAdd(acc + 2 * (size_t)r.layer, (unsigned long long)(long long)r.m);
+  atomicAdd(acc + 2 * (size_t)r.layer + 1, (unsigned long long)(long long)r.b);
+}
+
 // The other array's word w shifted by one site onto this word's sites, so
 // that each site meets its second z-neighbour: site j of array 0 meets site
 // j - 1 of array 1, site j of array 1 meets site j + 1 of array 0, and the
@@ -181,10 +275,11 @@ __device__ __forceinline__ uint32_t z_shifted(const FilmCtx& c, const Fetched& f
   return Zs;
 }
 
-template <bool FULL, bool FAST, bool QUARTER>
+template <bool FULL, bool FAST, bool QUARTER, bool MEAS = false>
 __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched& f,
                                                 const uint32_t* __restrict__ s_thr,
-                                                const uint32_t* __restrict__ s_alw, uint32_t qsel) {
+                                                const uint32_t* __restrict__ s_alw, uint32_t qsel,
+                                                uint32_t* stash = nullptr) {
   const uint32_t Lx = c.Lx, Ly = c.Ly;
   const uint32_t kx = f.kx, ky = f.ky, w = f.w;
   const uint32_t row = (kx - 1) * Ly + (ky - 1);
@@ -208,6 +303,7 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const uint32_t s2 = a3 ^ a4 ^ a5, k2 = maj3(a3, a4, a5);
   const uint32_t c0 = s1 ^ s2, k3 = s1 & s2;
   const uint32_t c1 = k1 ^ k2 ^ k3, c2 = maj3(k1, k2, k3);
+  if (MEAS) stash_counts(stash, c0, c1, c2, f.z0);  // for word_sums after the draws
 
   const uint32_t cls = row_class(kx, Lx);
   uint32_t alw = 0;
@@ -303,70 +399,6 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   return (lt | alw) & valid;
 }
 
-// Record sums of one word after its update to v (row (f.kx, f.ky), this
-// half-sweep's array X): the magnetisation of the row's two words w, and the
-// sum of sigma_b S_i S_j over the bonds from the word's sites to their six
-// neighbours (an empty x slot is no bond).  In half-sweep 1 every neighbour
-// word is final here -- it holds the other colour, or it is the wrap partner
-// this thread updated just before -- except the -y word of a ky = 1 row when
-// the seam joins one colour (its partner is updated after it); skip_ym
-// leaves that bond to the partner, which counts it from its +y side.
-struct LayerSums {
-  uint32_t layer = 0xFFFFFFFFu;  // 0-based kx, none when 0xFFFFFFFF
-  int m = 0, b = 0;
-};
-
-__device__ __forceinline__ LayerSums word_sums(const FilmCtx& c, const Fetched& f, uint32_t v, bool skip_ym) {
-  const uint32_t X = (f.kx + f.ky + 1 + c.colour) & 1u;
-  const bool last = f.w + 1 == c.W;
-  const uint32_t valid = last ? c.last_mask : 0xFFFFFFFFu;
-  const int nv = __popc(valid);
-  const uint32_t negm = (c.y_mode != kYPbc) ? 0xFFFFFFFFu : 0u;
-  const uint32_t Zs = (last && c.last_mask != 0xFFFFFFFFu) ? z_shifted<false>(c, f, X) : z_shifted<true>(c, f, X);
-  int pa = __popc(~(v ^ f.yp ^ (f.ky < c.Ly ? 0u : negm)) & valid) + __popc(~(v ^ f.z0) & valid) +
-           __popc(~(v ^ Zs) & valid);
-  int nd = 3;
-  if (f.kx > 1 || c.x_pbc) { pa += __popc(~(v ^ f.xm) & valid); nd++; }
-  if (f.kx < c.Lx || c.x_pbc) { pa += __popc(~(v ^ f.xp) & valid); nd++; }
-  if (!skip_ym) { pa += __popc(~(v ^ f.ym ^ (f.ky > 1 ? 0u : negm)) & valid); nd++; }
-  LayerSums r;
-  r.layer = f.kx - 1;
-  r.m = 2 * (__popc(v & valid) + __popc(f.z0 & valid)) - 2 * nv;
-  r.b = 2 * pa - nd * nv;
-  return r;
-}
-
-// The seam bonds between the other arrays of a ky = 1 row (its word f) and
-// its partner row (word g) when the seam joins one colour: neither end is
-// updated in half-sweep 1, so the thread that holds both counts them.
-__device__ __forceinline__ int seam_other_bonds(const FilmCtx& c, const Fetched& f, const Fetched& g) {
-  const uint32_t valid = (f.w + 1 == c.W) ? c.last_mask : 0xFFFFFFFFu;
-  const int s = __popc(valid) - 2 * __popc((f.z0 ^ g.z0) & valid);
-  return c.y_mode != kYPbc ? -s : s;
-}
-
-// Adds the sums of every lane that has some into the film's per-layer int64
-// accumulators [2 kx (magnetisation), 2 kx + 1 (bonds)].  All 32 lanes call
-// it.  A warp whose sums all fall in one layer adds them with two atomics,
-// otherwise each lane adds its own.  Integer atomics: exact in any order.
-__device__ __forceinline__ void add_layer_sums(unsigned long long* acc, const LayerSums& r) {
-  const bool on = r.layer != 0xFFFFFFFFu;
-  const uint32_t act = __ballot_sync(0xFFFFFFFFu, on);
-  if (act == 0) return;
-  const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, r.layer, __ffs(act) - 1);
-  if (__all_sync(0xFFFFFFFFu, !on || r.layer == l0)) {
-    const int m = __reduce_add_sync(0xFFFFFFFFu, on ? r.m : 0);
-    const int b = __reduce_add_sync(0xFFFFFFFFu, on ? r.b : 0);
-    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(act) - 1)) {
-      atomicAdd(acc + 2 * (size_t)l0, (unsigned long long)(long long)m);
-      atomicAdd(acc + 2 * (size_t)l0 + 1, (unsigned long long)(long long)b);
-    }
-  } else if (on) {
-    atomicAdd(acc + 2 * (size_t)r.layer, (unsigned long long)(long long)r.m);
-    atomicAdd(acc + 2 * (size_t)r.layer + 1, (unsigned long long)(long long)r.b);
-  }
-}
-
 __device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, uint32_t v) {
   const uint32_t row = (f.kx - 1) * c.Ly + (f.ky - 1);
   const uint32_t X = (f.kx + f.ky + 1 + c.colour) & 1u;
@@ -384,48 +416,54 @@ __device__ __forceinline__ void item_word(const FilmCtx& c, uint32_t item, uint3
 }
 
 // MEAS: also return the record sums of the word (r1) and of its partner word
-// (r2, ky = 1 only); see word_sums.
+// (r2, ky = 1 only), using the thread's stash slots.
 template <bool FAST, bool MEAS = false>
 __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
-                                               const uint32_t* s_alw, LayerSums* r1 = nullptr,
-                                               LayerSums* r2 = nullptr) {
+                                               const uint32_t* s_alw, uint32_t* stash = nullptr,
+                                               LayerSums* r1 = nullptr, LayerSums* r2 = nullptr) {
   const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
-  const uint32_t v = f.S ^ (full ? decide_word<true, FAST, false>(c, f, s_thr, s_alw, 0)
-                                 : decide_word<false, FAST, false>(c, f, s_thr, s_alw, 0));
+  const uint32_t fl = full ? decide_word<true, FAST, false, MEAS>(c, f, s_thr, s_alw, 0, stash)
+                           : decide_word<false, FAST, false, MEAS>(c, f, s_thr, s_alw, 0, stash);
+  const uint32_t v = f.S ^ fl;
   store_word(c, f, v);
-  if (MEAS) *r1 = word_sums(c, f, v, f.ky == 1 && c.seam_same);
+  if (MEAS) *r1 = word_sums(c, f.kx, f.w, fl, v, stash);
   // ky = 1 rows then update their wrap partner row (kx', Ly); its wrap
   // neighbour is the word just written, so it is fetched only now
   if (f.ky == 1) {
     const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
     Fetched g;
     fetch_word(c, kx2, c.Ly, f.w, g);
-    const uint32_t v2 = g.S ^ (full ? decide_word<true, FAST, false>(c, g, s_thr, s_alw, 0)
-                                    : decide_word<false, FAST, false>(c, g, s_thr, s_alw, 0));
+    if (MEAS) stash[4 * kFilmThreads] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3 * kFilmThreads], g) : 0u;
+    const uint32_t fl2 = full ? decide_word<true, FAST, false, MEAS>(c, g, s_thr, s_alw, 0, stash)
+                              : decide_word<false, FAST, false, MEAS>(c, g, s_thr, s_alw, 0, stash);
+    const uint32_t v2 = g.S ^ fl2;
     store_word(c, g, v2);
     if (MEAS) {
-      *r2 = word_sums(c, g, v2, false);
-      if (c.seam_same) r2->b += seam_other_bonds(c, f, g);
+      *r2 = word_sums(c, kx2, g.w, fl2, v2, stash);
+      r2->b += (int)stash[4 * kFilmThreads];
     }
   }
 }
 
 // The same for a word shared by the four lanes 4j..4j+3 of a warp (lane qsel
 // draws Philox calls qsel and qsel + 4); gmask holds the lanes whose group has
-// a word.  The lanes merge their flip masks and the group's lane 0 stores.
+// a word.  The lanes merge their flip masks and the group's lane 0 stores
+// (and, MEAS, takes the record sums).
 template <bool FAST, bool MEAS>
 __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const Fetched& f, bool on, uint32_t qsel,
                                                        uint32_t gmask, const uint32_t* s_thr,
-                                                       const uint32_t* s_alw, LayerSums& r1, LayerSums& r2) {
+                                                       const uint32_t* s_alw, uint32_t* stash, LayerSums& r1,
+                                                       LayerSums& r2) {
   const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
   uint32_t fl = 0;
-  if (on) fl = full ? decide_word<true, FAST, true>(c, f, s_thr, s_alw, qsel)
-                    : decide_word<false, FAST, true>(c, f, s_thr, s_alw, qsel);
+  if (on) fl = full ? decide_word<true, FAST, true, MEAS>(c, f, s_thr, s_alw, qsel, stash)
+                    : decide_word<false, FAST, true, MEAS>(c, f, s_thr, s_alw, qsel, stash);
   if (!on) return;
   fl |= __shfl_xor_sync(gmask, fl, 1);
   fl |= __shfl_xor_sync(gmask, fl, 2);
-  if (qsel == 0) store_word(c, f, f.S ^ fl);
-  if (MEAS && qsel == 0) r1 = word_sums(c, f, f.S ^ fl, f.ky == 1 && c.seam_same);
+  const uint32_t v = f.S ^ fl;
+  if (qsel == 0) store_word(c, f, v);
+  if (MEAS && qsel == 0) r1 = word_sums(c, f.kx, f.w, fl, v, stash);
   // ky = 1 words then update their wrap partner word (see update_fetched)
   const uint32_t pmask = __ballot_sync(gmask, f.ky == 1);
   if (f.ky != 1) return;
@@ -433,14 +471,16 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
   const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
   Fetched g;
   fetch_word(c, kx2, c.Ly, f.w, g);
-  uint32_t fl2 = full ? decide_word<true, FAST, true>(c, g, s_thr, s_alw, qsel)
-                      : decide_word<false, FAST, true>(c, g, s_thr, s_alw, qsel);
+  if (MEAS) stash[4 * kFilmThreads] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3 * kFilmThreads], g) : 0u;
+  uint32_t fl2 = full ? decide_word<true, FAST, true, MEAS>(c, g, s_thr, s_alw, qsel, stash)
+                      : decide_word<false, FAST, true, MEAS>(c, g, s_thr, s_alw, qsel, stash);
   fl2 |= __shfl_xor_sync(pmask, fl2, 1);
   fl2 |= __shfl_xor_sync(pmask, fl2, 2);
-  if (qsel == 0) store_word(c, g, g.S ^ fl2);
+  const uint32_t v2 = g.S ^ fl2;
+  if (qsel == 0) store_word(c, g, v2);
   if (MEAS && qsel == 0) {
-    r2 = word_sums(c, g, g.S ^ fl2, false);
-    if (c.seam_same) r2.b += seam_other_bonds(c, f, g);
+    r2 = word_sums(c, kx2, g.w, fl2, v2, stash);
+    r2.b += (int)stash[4 * kFilmThreads];
   }
 }
 
@@ -450,12 +490,14 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
 // thread fetches its ITEMS words (kFilmThreads apart) before deciding any;
 // ITEMS = 0: four lanes per word (kFilmThreads / 4 words).  MEAS and acc set
 // (half-sweep 1 of a sweep after which the film records): the words' record
-// sums go into the film's per-layer accumulators acc.
+// sums go into the film's per-layer accumulators acc; s_stash holds
+// kStashSlots words per thread.
 template <bool FAST, uint32_t ITEMS, bool MEAS>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw,
-                                            unsigned long long* acc) {
+                                            unsigned long long* acc, uint32_t* s_stash) {
+  uint32_t* stash = s_stash + threadIdx.x;
   if (ITEMS == 0) {
     const uint32_t item = first + (threadIdx.x >> 2);
     const bool on = item < items;
@@ -468,11 +510,11 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
     }
     LayerSums r1, r2;
     if (MEAS && acc) {
-      update_fetched_quarter<FAST, true>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, r1, r2);
+      update_fetched_quarter<FAST, true>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, stash, r1, r2);
       add_layer_sums(acc, r1);
-      add_layer_sums(acc, r2);
+      add_lane_sums(acc, r2);
     } else {
-      update_fetched_quarter<FAST, false>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, r1, r2);
+      update_fetched_quarter<FAST, false>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, stash, r1, r2);
     }
     return;
   }
@@ -493,9 +535,9 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 #pragma unroll
     for (uint32_t it = 0; it < NI; it++) {
       LayerSums r1, r2;
-      if (mine[it]) update_fetched<FAST, true>(c, fw[it], s_thr, s_alw, &r1, &r2);
+      if (mine[it]) update_fetched<FAST, true>(c, fw[it], s_thr, s_alw, stash, &r1, &r2);
       add_layer_sums(acc, r1);
-      add_layer_sums(acc, r2);
+      add_lane_sums(acc, r2);
     }
     return;
   }
@@ -512,7 +554,7 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // half-sweep 1 launch of a sweep after which some film records; those films
 // add their record sums into their accumulators in `part`.
 template <bool FAST, uint32_t ITEMS, bool MEAS>
-__global__ void __launch_bounds__(kFilmThreads, ((FAST || ITEMS < 2) && !MEAS) ? kMultiMinBlocks : kMultiMinBlocks - 1)
+__global__ void __launch_bounds__(kFilmThreads, (FAST || ITEMS < 2) ? kMultiMinBlocks : kMultiMinBlocks - 1)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k,
               int64_t* __restrict__ part) {
@@ -521,6 +563,7 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
   __shared__ __align__(16) FilmDesc s_d;
   __shared__ __align__(16) uint32_t s_alw[FAST ? 1 : 64];
   __shared__ __align__(16) uint32_t s_lo[64];
+  __shared__ uint32_t s_stash[MEAS ? kStashSlots * kFilmThreads : 1];
   pdl_trigger();
   pdl_wait();
   const uint32_t nvb = hdr->upd_blocks;
@@ -552,7 +595,7 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
       acc = reinterpret_cast<unsigned long long*>(part + acc_offset(s_d));
     const uint32_t first = (vb - s_d.upd_block_begin) * words_per_block(ITEMS);
     sweep_block<FAST, ITEMS, MEAS>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
-                                   s_alw, acc);
+                                   s_alw, acc, s_stash);
   }
 }
 
@@ -562,12 +605,13 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
 // onwards.  MEAS: half-sweep 1 before a record, whose sums go into the
 // film's accumulators acc.
 template <bool FAST, uint32_t ITEMS, bool MEAS>
-__global__ void __launch_bounds__(kFilmThreads, MEAS ? kFilmMinBlocks - 1 : kFilmMinBlocks)
+__global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
 update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
                    uint32_t sweep, int64_t* __restrict__ acc) {
   pdl_trigger();
   __shared__ __align__(16) uint32_t s_thr[64];
   __shared__ __align__(16) uint32_t s_alw[64];
+  __shared__ uint32_t s_stash[MEAS ? kStashSlots * kFilmThreads : 1];
   for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
     const bool a = (d.always[i >> 4] >> (i & 15)) & 1u;
     s_thr[i] = FAST ? (a ? 0xFFFFFFFFu : d.thr[i >> 4][i & 15] - 1u) : d.thr[i >> 4][i & 15];
@@ -585,7 +629,8 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
   c.seam_same = seam_joins_one_colour(d.Lx, d.Ly, d.y_mode);
   sweep_block<FAST, ITEMS, MEAS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
-                                 d.divy_l, s_thr, s_alw, MEAS ? reinterpret_cast<unsigned long long*>(acc) : nullptr);
+                                 d.divy_l, s_thr, s_alw, MEAS ? reinterpret_cast<unsigned long long*>(acc) : nullptr,
+                                 s_stash);
 }
 
 // ------------------------------------------------------------ measurement
