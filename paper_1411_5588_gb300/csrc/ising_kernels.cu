@@ -120,11 +120,15 @@ __host__ __device__ inline uint32_t seam_joins_one_colour(uint32_t Lx, uint32_t 
   return y_mode == kYGapbc ? ((Lx + Ly) % 2 == 0) : (Ly % 2 == 1);
 }
 
-// Whether film F records after `done` sweeps of the current chunk.
+// Whether film F, at chunk start sweep `sweep`, records after `done` sweeps
+// of the chunk.
+__device__ __forceinline__ bool records_after(const FilmDesc& F, uint32_t sweep, uint32_t done) {
+  if (F.measure_every == 0 || done == 0 || F.sweep_end - sweep < done) return false;
+  return ((sweep + done) % F.measure_every) == 0;
+}
+
 __device__ __forceinline__ bool measured_now(const FilmDesc& F, uint32_t done, int force) {
-  if (force) return true;
-  if (F.measure_every == 0 || done == 0 || F.sweep_end - F.sweep < done) return false;
-  return ((F.sweep + done) % F.measure_every) == 0;
+  return force || records_after(F, F.sweep, done);
 }
 
 // The words one thread needs to update word w of row (kx, ky), loaded ahead
@@ -488,15 +492,16 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
 
 // The words of one block of words_per_block(ITEMS) consecutive words: each
 // thread fetches its ITEMS words (kFilmThreads apart) before deciding any;
-// ITEMS = 0: four lanes per word (kFilmThreads / 4 words).  MEAS and acc set
+// ITEMS = 0: four lanes per word (kFilmThreads / 4 words).  MEAS and meas
 // (half-sweep 1 of a sweep after which the film records): the words' record
-// sums go into the film's per-layer accumulators acc; s_stash holds
-// kStashSlots words per thread.
-template <bool FAST, uint32_t ITEMS, bool MEAS>
+// sums go into the film's per-layer accumulators acc_of() (a pointer made
+// where it is used, not kept across the draws); s_stash holds kStashSlots
+// words per thread.
+template <bool FAST, uint32_t ITEMS, bool MEAS, typename AccOf>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw,
-                                            unsigned long long* acc, uint32_t* s_stash) {
+                                            bool meas, AccOf acc_of, uint32_t* s_stash) {
   uint32_t* stash = s_stash + threadIdx.x;
   if (ITEMS == 0) {
     const uint32_t item = first + (threadIdx.x >> 2);
@@ -509,10 +514,10 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
       fetch_word(c, kx, ky, w, f);
     }
     LayerSums r1, r2;
-    if (MEAS && acc) {
+    if (MEAS && meas) {
       update_fetched_quarter<FAST, true>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, stash, r1, r2);
-      add_layer_sums(acc, r1);
-      add_lane_sums(acc, r2);
+      add_layer_sums(acc_of(), r1);
+      add_lane_sums(acc_of(), r2);
     } else {
       update_fetched_quarter<FAST, false>(c, f, on, threadIdx.x & 3u, gmask, s_thr, s_alw, stash, r1, r2);
     }
@@ -531,13 +536,13 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
       fetch_word(c, kx, ky, w, fw[it]);
     }
   }
-  if (MEAS && acc) {
+  if (MEAS && meas) {
 #pragma unroll
     for (uint32_t it = 0; it < NI; it++) {
       LayerSums r1, r2;
       if (mine[it]) update_fetched<FAST, true>(c, fw[it], s_thr, s_alw, stash, &r1, &r2);
-      add_layer_sums(acc, r1);
-      add_lane_sums(acc, r2);
+      add_layer_sums(acc_of(), r1);
+      add_lane_sums(acc_of(), r2);
     }
     return;
   }
@@ -550,11 +555,12 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // words of film owner[b], whose descriptor is staged in shared memory.  FAST:
 // no film of the launch has a reachable thr = 0 entry (the compare-only
 // table); otherwise every film takes the exact variant (which, at two words
-// per thread, needs the registers of one block per SM fewer).  MEAS: the
-// half-sweep 1 launch of a sweep after which some film records; those films
-// add their record sums into their accumulators in `part`.
+// per thread, needs the registers of one block per SM fewer, and so does its
+// recording form at one word).  MEAS: the half-sweep 1 launch of a sweep
+// after which some film records; those films add their record sums into
+// their accumulators in `part`.
 template <bool FAST, uint32_t ITEMS, bool MEAS>
-__global__ void __launch_bounds__(kFilmThreads, (FAST || ITEMS < 2) ? kMultiMinBlocks : kMultiMinBlocks - 1)
+__global__ void __launch_bounds__(kFilmThreads, (FAST || (ITEMS < 2 && !MEAS)) ? kMultiMinBlocks : kMultiMinBlocks - 1)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k,
               int64_t* __restrict__ part) {
@@ -565,7 +571,6 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
   __shared__ __align__(16) uint32_t s_lo[64];
   __shared__ uint32_t s_stash[MEAS ? kStashSlots * kFilmThreads : 1];
   pdl_trigger();
-  pdl_wait();
   const uint32_t nvb = hdr->upd_blocks;
   for (uint32_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
     const uint32_t f = owner[vb];  // the same for every thread of the block
@@ -580,7 +585,17 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
       s_lo[i] = FAST ? (a ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
     }
     __syncthreads();
-    if (!s_d.active || s_d.sweep + k >= s_d.sweep_end) continue;
+    if (!s_d.active) continue;
+    // The owner table, the descriptor and the table above are written by the
+    // host before the launch; the lattice and the film's sweep counter may
+    // still be written by the previous kernel of the stream (its blocks run
+    // while these stage).  Wait for it (a no-op after the first time), then
+    // read the counter again, around L1 (the staged copy may predate the
+    // wait).
+    pdl_wait();
+    if (threadIdx.x == 0) s_d.sweep = __ldcg(&films[f].sweep);
+    __syncthreads();
+    if (s_d.sweep + k >= s_d.sweep_end) continue;
     FilmCtx c;
     c.Lx = s_d.Lx; c.Ly = s_d.Ly; c.n = s_d.n; c.W = s_d.W; c.Wp = s_d.Wp;
     c.plane_words = s_d.Lx * s_d.Ly * s_d.Wp;
@@ -590,12 +605,12 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     c.plane0 = pool + s_d.spin_off;
     c.plane1 = c.plane0 + (size_t)c.Lx * c.Ly * c.Wp;
     c.seam_same = seam_joins_one_colour(c.Lx, c.Ly, c.y_mode);
-    unsigned long long* acc = nullptr;
-    if (MEAS && colour == 1 && measured_now(s_d, k + 1, 0))
-      acc = reinterpret_cast<unsigned long long*>(part + acc_offset(s_d));
+    const bool meas = MEAS && colour == 1 && measured_now(s_d, k + 1, 0);
+    const FilmDesc* sd = &s_d;
+    auto acc_of = [part, sd]() { return reinterpret_cast<unsigned long long*>(part + acc_offset(*sd)); };
     const uint32_t first = (vb - s_d.upd_block_begin) * words_per_block(ITEMS);
     sweep_block<FAST, ITEMS, MEAS>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
-                                   s_alw, acc, s_stash);
+                                   s_alw, meas, acc_of, s_stash);
   }
 }
 
@@ -628,9 +643,9 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   c.plane0 = pool + d.spin_off;
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
   c.seam_same = seam_joins_one_colour(d.Lx, d.Ly, d.y_mode);
+  auto acc_of = [acc]() { return reinterpret_cast<unsigned long long*>(acc); };
   sweep_block<FAST, ITEMS, MEAS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
-                                 d.divy_l, s_thr, s_alw, MEAS ? reinterpret_cast<unsigned long long*>(acc) : nullptr,
-                                 s_stash);
+                                 d.divy_l, s_thr, s_alw, MEAS, acc_of, s_stash);
 }
 
 // ------------------------------------------------------------ measurement
