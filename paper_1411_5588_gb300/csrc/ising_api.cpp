@@ -192,6 +192,7 @@ int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_g
   const uint32_t fg = fixed_grid ? (uint32_t)(2 * n_sm) : fin_grid();
   bool exact = false;
   for (const auto& d : h) exact = exact || (d.active && d.has_never);
+  bool prev_meas = false;
   for (uint32_t k = k0; k < k0 + n; k++) {
     bool meas = all_meas;
     if (!meas)
@@ -201,10 +202,12 @@ int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_g
           meas = true;
           break;
         }
-    // records: half-sweep 1 accumulates the sums, a small kernel writes them
-    ISG_CK(launch_update(L, ug, pool, 0, k, exact, items, nullptr, stream));
-    ISG_CK(launch_update(L, ug, pool, 1, k, exact, items, meas ? part : nullptr, stream));
-    if (meas) ISG_CK(launch_record(L, fg, part, rec, k + 1, stream));
+    // records: half-sweep 1 accumulates the sums; the next half-sweep 0
+    // writes them, or, after the last sweep of the call, a small kernel
+    ISG_CK(launch_update(L, ug, pool, 0, k, exact, items, part, rec, false, prev_meas ? k : 0, stream));
+    ISG_CK(launch_update(L, ug, pool, 1, k, exact, items, part, rec, meas, 0, stream));
+    if (meas && k + 1 == k0 + n) ISG_CK(launch_record(L, fg, part, rec, k + 1, stream));
+    prev_meas = meas;
   }
   return ISING_OK;
 }

@@ -170,6 +170,57 @@ __device__ __forceinline__ void fetch_word(const FilmCtx& c, uint32_t kx, uint32
 // the mask of sites that flip.  QUARTER: only Philox calls qsel and qsel + 4
 // (the sites at bits qsel and qsel + 4 of each byte), for a word shared by
 // four lanes.
+__device__ __forceinline__ int64_t block_sum(int64_t v, int64_t* s_red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  int64_t t = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += s_red[i];
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// The record of film Fg after `done` sweeps of the chunk (chunk-start sweep
+// `sweep`), from the per-layer accumulators half-sweep 1 filled, which it
+// clears; advances the film's ring counter.  F holds the film's static
+// fields (a staged copy or Fg itself).  The whole block calls it; s_red holds
+// one int64 per warp.
+__device__ __noinline__ void write_record(FilmDesc* Fg, const FilmDesc& F, uint32_t sweep, int64_t* part,
+                                             int64_t* records, uint32_t done, int64_t* s_red, uint32_t* s_slot) {
+  const uint32_t Lx = F.Lx;
+  uint32_t rn = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    rn = __ldcg(&Fg->rec_next);  // written by an earlier kernel
+    *s_slot = F.rec_cap ? rn % F.rec_cap : 0u;
+  }
+  __syncthreads();
+  int64_t* rec = records + F.rec_off + (size_t)*s_slot * (5 + Lx);
+  int64_t* acc = part + acc_offset(F);
+  int64_t M = 0, Bs = 0;
+  for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) {
+    const int64_t m = acc[2 * kx], b = acc[2 * kx + 1];
+    acc[2 * kx] = 0;
+    acc[2 * kx + 1] = 0;
+    rec[5 + kx] = m;
+    M += m;
+    Bs += b;
+  }
+  const int64_t tM = block_sum(M, s_red);
+  const int64_t tB = block_sum(Bs, s_red);
+  if (threadIdx.x == 0) {
+    rec[0] = (int64_t)sweep + done;
+    rec[1] = tB;
+    rec[2] = tM;
+    rec[3] = rec[5];
+    rec[4] = rec[5 + Lx - 1];
+    Fg->rec_next = rn + 1;
+  }
+}
+
 // Record sums of half-sweep 1.  After its update every neighbour word a
 // thread loaded is final -- it holds the other colour -- except the -y word
 // of a ky = 1 row when the seam joins one colour: that is its wrap partner,
@@ -556,20 +607,29 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // no film of the launch has a reachable thr = 0 entry (the compare-only
 // table); otherwise every film takes the exact variant (which, at two words
 // per thread, needs the registers of one block per SM fewer, and so does its
-// recording form at one word).  MEAS: the half-sweep 1 launch of a sweep
-// after which some film records; those films add their record sums into
-// their accumulators in `part`.
-template <bool FAST, uint32_t ITEMS, bool MEAS>
-__global__ void __launch_bounds__(kFilmThreads, (FAST || (ITEMS < 2 && !MEAS)) ? kMultiMinBlocks : kMultiMinBlocks - 1)
+// recording form at one word).  MODE kUpdAccumulate: the half-sweep 1 launch
+// of a sweep after which some film records; those films add their record
+// sums into their accumulators in `part`.  MODE kUpdWriteRecord: a half-sweep
+// 0 launch right after such a sweep; the first block of each film that
+// recorded after `rec_done` sweeps writes that record (write_record) before
+// its update, so the write overlaps the launch's other blocks.
+enum : uint32_t { kUpdPlain = 0, kUpdAccumulate = 1, kUpdWriteRecord = 2 };
+
+template <bool FAST, uint32_t ITEMS, uint32_t MODE>
+__global__ void __launch_bounds__(kFilmThreads, (FAST || (ITEMS < 2 && MODE != kUpdAccumulate))
+                                                    ? kMultiMinBlocks : kMultiMinBlocks - 1)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k,
-              int64_t* __restrict__ part) {
+              int64_t* __restrict__ part, int64_t* __restrict__ records, uint32_t rec_done) {
+  constexpr bool MEAS = MODE == kUpdAccumulate;
   constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
   static_assert(sizeof(FilmDesc) % 16 == 0, "descriptor copied as uint4");
   __shared__ __align__(16) FilmDesc s_d;
   __shared__ __align__(16) uint32_t s_alw[FAST ? 1 : 64];
   __shared__ __align__(16) uint32_t s_lo[64];
   __shared__ uint32_t s_stash[MEAS ? kStashSlots * kFilmThreads : 1];
+  __shared__ int64_t s_red[MODE == kUpdWriteRecord ? kFilmThreads / 32 : 1];
+  __shared__ uint32_t s_slot;
   pdl_trigger();
   const uint32_t nvb = hdr->upd_blocks;
   for (uint32_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
@@ -595,6 +655,8 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     pdl_wait();
     if (threadIdx.x == 0) s_d.sweep = __ldcg(&films[f].sweep);
     __syncthreads();
+    if (MODE == kUpdWriteRecord && vb == s_d.upd_block_begin && records_after(s_d, s_d.sweep, rec_done))
+      write_record(const_cast<FilmDesc*>(films + f), s_d, s_d.sweep, part, records, rec_done, s_red, &s_slot);
     if (s_d.sweep + k >= s_d.sweep_end) continue;
     FilmCtx c;
     c.Lx = s_d.Lx; c.Ly = s_d.Ly; c.n = s_d.n; c.W = s_d.W; c.Wp = s_d.Wp;
@@ -651,19 +713,6 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
 // ------------------------------------------------------------ measurement
 
 namespace {
-
-__device__ __forceinline__ int64_t block_sum(int64_t v, int64_t* s_red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) s_red[warp] = v;
-  __syncthreads();
-  int64_t t = 0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += s_red[i];
-  __syncthreads();
-  return t;  // valid in thread 0
-}
 
 __device__ __forceinline__ int bonds(uint32_t a, uint32_t b, uint32_t valid, int nv) {
   return nv - 2 * __popc((a ^ b) & valid);
@@ -847,31 +896,7 @@ record_kernel(FilmDesc* __restrict__ films, const LaunchHdr* __restrict__ hdr, i
   for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
     FilmDesc& F = films[f];
     if (!F.active || !measured_now(F, done, 0)) continue;
-    const uint32_t Lx = F.Lx;
-    __syncthreads();
-    if (threadIdx.x == 0) s_slot = F.rec_cap ? (F.rec_next % F.rec_cap) : 0u;
-    __syncthreads();
-    int64_t* rec = records + F.rec_off + (size_t)s_slot * (5 + Lx);
-    int64_t* acc = part + acc_offset(F);
-    int64_t M = 0, Bs = 0;
-    for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) {
-      const int64_t m = acc[2 * kx], b = acc[2 * kx + 1];
-      acc[2 * kx] = 0;
-      acc[2 * kx + 1] = 0;
-      rec[5 + kx] = m;
-      M += m;
-      Bs += b;
-    }
-    const int64_t tM = block_sum(M, s_red);
-    const int64_t tB = block_sum(Bs, s_red);
-    if (threadIdx.x == 0) {
-      rec[0] = (int64_t)F.sweep + done;
-      rec[1] = tB;
-      rec[2] = tM;
-      rec[3] = rec[5];
-      rec[4] = rec[5 + Lx - 1];
-      F.rec_next = F.rec_next + 1;
-    }
+    write_record(&F, F, F.sweep, part, records, done, s_red, &s_slot);
   }
 }
 
@@ -1105,12 +1130,12 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, 
 
 namespace {
 
-template <bool MEAS>
+template <uint32_t MODE>
 auto update_variant(bool exact, uint32_t items) {
-  return exact ? (items == 2 ? update_kernel<false, 2, MEAS>
-                             : items == 1 ? update_kernel<false, 1, MEAS> : update_kernel<false, 0, MEAS>)
-               : (items == 2 ? update_kernel<true, 2, MEAS>
-                             : items == 1 ? update_kernel<true, 1, MEAS> : update_kernel<true, 0, MEAS>);
+  return exact ? (items == 2 ? update_kernel<false, 2, MODE>
+                             : items == 1 ? update_kernel<false, 1, MODE> : update_kernel<false, 0, MODE>)
+               : (items == 2 ? update_kernel<true, 2, MODE>
+                             : items == 1 ? update_kernel<true, 1, MODE> : update_kernel<true, 0, MODE>);
 }
 
 template <bool MEAS>
@@ -1124,11 +1149,14 @@ auto update_film_variant(bool exact, uint32_t items) {
 }  // namespace
 
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          uint32_t items, int64_t* part, cudaStream_t st) {
+                          uint32_t items, int64_t* part, int64_t* records, bool accumulate, uint32_t rec_done,
+                          cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  auto* kern = part ? update_variant<true>(exact, items) : update_variant<false>(exact, items);
+  auto* kern = (accumulate && colour == 1) ? update_variant<kUpdAccumulate>(exact, items)
+               : (rec_done && colour == 0) ? update_variant<kUpdWriteRecord>(exact, items)
+                                           : update_variant<kUpdPlain>(exact, items);
   return launch_pdl(kern, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
-                    (const LaunchHdr*)L.hdr, pool, colour, k, part);
+                    (const LaunchHdr*)L.hdr, pool, colour, k, part, records, rec_done);
 }
 
 cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep, uint32_t items,
@@ -1218,7 +1246,8 @@ int read_oob_counters(unsigned long long* count, unsigned long long* first) {
 
 int update_blocks_per_sm() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<true, 1, false>, kFilmThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<true, 1, kUpdPlain>, kFilmThreads, 0) !=
+      cudaSuccess)
     return 0;
   return nb;
 }

@@ -63,11 +63,14 @@ struct LaunchSet {
 
 // exact: some film of the launch has a reachable thr = 0 entry (has_never);
 // items: words per thread (1 or 2, or 0 for four lanes per word), matching the
-// owner table's block size.  part (colour 1 only, else null): the films that
-// record after sweep k add their record sums into their accumulators there;
-// launch_record then writes the records.
+// owner table's block size.  Records: with accumulate (colour 1) the films
+// that record after sweep k add their record sums into their accumulators in
+// part; with rec_done > 0 (colour 0) the films that recorded after rec_done
+// sweeps have that record written into their rings in records by this
+// launch (the chunk's last record goes through launch_record instead).
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          uint32_t items, int64_t* part, cudaStream_t st);
+                          uint32_t items, int64_t* part, int64_t* records, bool accumulate, uint32_t rec_done,
+                          cudaStream_t st);
 // One half-sweep of a single film whose descriptor (with `sweep` absolute) is
 // passed by value; acc (colour 1 of a recorded sweep, else null): the film's
 // accumulators.
