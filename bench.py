@@ -167,8 +167,19 @@ def cpu_baseline(min_seconds=10.0, max_sweeps=40):
         n += 1
     dt = time.perf_counter() - t0
     att = WL.sites(job) * n
-    return {"value": att / dt / 1e9, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
-            "sample": f"{n} sweeps of the 120x240x1600 film after its slab start ({att} attempts, {dt:.1f} s)"}
+    cores = O.get_threads()
+    # the same oracle on one core, continuing the chain (two sweeps)
+    O.set_threads(1)
+    t1 = time.perf_counter()
+    for _ in range(2):
+        f.sweep(1, 0)
+    d1 = time.perf_counter() - t1
+    O.set_threads(ncores)
+    a1 = WL.sites(job) * 2
+    return {"value": att / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} sweeps of the 120x240x1600 film after its slab start ({att} attempts, {dt:.1f} s)",
+            "single_core": {"value": a1 / d1 / 1e9, "unit": UNIT, "cores": 1,
+                            "sample": f"the next 2 sweeps on one thread ({a1} attempts, {d1:.1f} s)"}}
 
 
 def reference_arm(args):
