@@ -236,7 +236,8 @@ __device__ __noinline__ void write_record(FilmDesc* Fg, const FilmDesc& F, uint3
 //   sum_d popc(a'_d) = n_old + D popc(fl) - 2 n_fl,
 // n_old and n_fl being the aligned counts summed over the valid and over the
 // flipped sites.  decide_word parks c0, c1, c2 and the row's other word z0 in
-// the thread's shared-memory slots (stride kFilmThreads) across the Philox
+// the thread's kStashSlots consecutive shared-memory words (thread-major; the
+// odd stride keeps a warp's accesses on distinct banks) across the Philox
 // draws, so the sums cost no registers there.
 constexpr uint32_t kStashSlots = 5;
 
@@ -247,9 +248,9 @@ struct LayerSums {
 
 __device__ __forceinline__ void stash_counts(uint32_t* stash, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t z0) {
   stash[0] = c0;
-  stash[kFilmThreads] = c1;
-  stash[2 * kFilmThreads] = c2;
-  stash[3 * kFilmThreads] = z0;
+  stash[1] = c1;
+  stash[2] = c2;
+  stash[3] = z0;
 }
 
 // Sums of the word of layer kx (1-based) whose flips were fl and whose new
@@ -258,8 +259,8 @@ __device__ __forceinline__ LayerSums word_sums(const FilmCtx& c, uint32_t kx, ui
                                                const uint32_t* stash) {
   const uint32_t valid = (w + 1 == c.W) ? c.last_mask : 0xFFFFFFFFu;
   const int nv = __popc(valid);
-  const uint32_t c0 = stash[0], c1 = stash[kFilmThreads], c2 = stash[2 * kFilmThreads];
-  const uint32_t z0 = stash[3 * kFilmThreads];
+  const uint32_t c0 = stash[0], c1 = stash[1], c2 = stash[2];
+  const uint32_t z0 = stash[3];
   const int D = 4 + ((kx > 1 || c.x_pbc) ? 1 : 0) + ((kx < c.Lx || c.x_pbc) ? 1 : 0);
   const int n_old = __popc(c0 & valid) + 2 * __popc(c1 & valid) + 4 * __popc(c2 & valid);
   const int n_fl = __popc(c0 & fl) + 2 * __popc(c1 & fl) + 4 * __popc(c2 & fl);
@@ -313,6 +314,28 @@ __device__ __forceinline__ void add_lane_sums(unsigned long long* acc, const Lay
   if (r.layer == 0xFFFFFFFFu) return;
   atomicAdd(acc + 2 * (size_t)r.layer, (unsigned long long)(long long)r.m);
   atomicAdd(acc + 2 * (size_t)r.layer + 1, (unsigned long long)(long long)r.b);
+}
+
+// The same into a block's shared counters (resident films: int32 suffices
+// below 2^16 sites): layer sums s_m[kx], and the totals s_tot = {B, M}.  All
+// 32 lanes call it.
+__device__ __forceinline__ void add_layer_sums_shared(int* s_m, int* s_tot, const LayerSums& r) {
+  const bool on = r.layer != 0xFFFFFFFFu;
+  const uint32_t act = __ballot_sync(0xFFFFFFFFu, on);
+  if (act == 0) return;
+  const int lead = __ffs(act) - 1;
+  const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, r.layer, lead);
+  const bool in0 = on && r.layer == l0;
+  const int m0 = __reduce_add_sync(0xFFFFFFFFu, in0 ? r.m : 0);
+  const int b = __reduce_add_sync(0xFFFFFFFFu, on ? r.b : 0);
+  const int m = __reduce_add_sync(0xFFFFFFFFu, on ? r.m : 0);
+  if ((int)(threadIdx.x & 31u) == lead) {
+    atomicAdd(&s_m[l0], m0);
+    atomicAdd(&s_tot[0], b);
+    atomicAdd(&s_tot[1], m);
+  } else if (on && !in0) {
+    atomicAdd(&s_m[r.layer], r.m);
+  }
 }
 
 // The other array's word w shifted by one site onto this word's sites, so
@@ -488,14 +511,14 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
     const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
     Fetched g;
     fetch_word(c, kx2, c.Ly, f.w, g);
-    if (MEAS) stash[4 * kFilmThreads] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3 * kFilmThreads], g) : 0u;
+    if (MEAS) stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3], g) : 0u;
     const uint32_t fl2 = full ? decide_word<true, FAST, false, MEAS>(c, g, s_thr, s_alw, 0, stash)
                               : decide_word<false, FAST, false, MEAS>(c, g, s_thr, s_alw, 0, stash);
     const uint32_t v2 = g.S ^ fl2;
     store_word(c, g, v2);
     if (MEAS) {
       *r2 = word_sums(c, kx2, g.w, fl2, v2, stash);
-      r2->b += (int)stash[4 * kFilmThreads];
+      r2->b += (int)stash[4];
     }
   }
 }
@@ -526,7 +549,7 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
   const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
   Fetched g;
   fetch_word(c, kx2, c.Ly, f.w, g);
-  if (MEAS) stash[4 * kFilmThreads] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3 * kFilmThreads], g) : 0u;
+  if (MEAS) stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3], g) : 0u;
   uint32_t fl2 = full ? decide_word<true, FAST, true, MEAS>(c, g, s_thr, s_alw, qsel, stash)
                       : decide_word<false, FAST, true, MEAS>(c, g, s_thr, s_alw, qsel, stash);
   fl2 |= __shfl_xor_sync(pmask, fl2, 1);
@@ -535,7 +558,7 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
   if (qsel == 0) store_word(c, g, v2);
   if (MEAS && qsel == 0) {
     r2 = word_sums(c, kx2, g.w, fl2, v2, stash);
-    r2.b += (int)stash[4 * kFilmThreads];
+    r2.b += (int)stash[4];
   }
 }
 
@@ -553,7 +576,7 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw,
                                             bool meas, AccOf acc_of, uint32_t* s_stash) {
-  uint32_t* stash = s_stash + threadIdx.x;
+  uint32_t* stash = s_stash + threadIdx.x * kStashSlots;
   if (ITEMS == 0) {
     const uint32_t item = first + (threadIdx.x >> 2);
     const bool on = item < items;
@@ -926,7 +949,8 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
   __shared__ __align__(16) FilmDesc s_d;
   __shared__ __align__(16) uint32_t s_thr[64];
   __shared__ __align__(16) uint32_t s_alw[64];
-  __shared__ int64_t s_red[kResidentThreads / 32];
+  __shared__ uint32_t s_stash[kStashSlots * kResidentThreads];
+  __shared__ int s_tot[2];  // B and M of the record being summed
   pdl_trigger();
   pdl_wait();
   FilmDesc* Fg = films + blockIdx.x;
@@ -952,6 +976,8 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
     const uint32_t rw = i - X * words, r = rw / W, w = rw - r * W;
     s_planes[i] = ISG_LD(X ? g1 : g0, (size_t)r * Wp + w, (size_t)Lx * Ly * Wp, 41);
   }
+  for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) s_m[kx] = 0;
+  if (threadIdx.x < 2) s_tot[threadIdx.x] = 0;
   __syncthreads();
   FilmCtx c;
   c.Lx = Lx; c.Ly = Ly; c.n = s_d.n; c.W = W; c.Wp = W;
@@ -969,62 +995,58 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
     const uint32_t t = s_d.sweep + k;
     if (t >= s_d.sweep_end) break;
     c.sweep = t;
+    // half-sweep 1 of a sweep after which the film records also sums the
+    // record (as the grid kernels do) into s_m and s_tot
+    const bool rec_now = m_every != 0 && (t + 1) % m_every == 0;
     for (uint32_t colour = 0; colour < 2; colour++) {
       c.colour = colour;
-      for (uint32_t item = threadIdx.x; item < items; item += blockDim.x) {
-        uint32_t kx, ky, w;
-        item_word(c, item, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, kx, ky, w);
-        Fetched f;
-        fetch_word(c, kx, ky, w, f);
-        update_fetched<FAST>(c, f, s_thr, s_alw);
+      if (colour == 1 && rec_now) {
+        uint32_t* stash = s_stash + threadIdx.x * kStashSlots;
+        for (uint32_t base = 0; base < items; base += blockDim.x) {
+          const uint32_t item = base + threadIdx.x;
+          LayerSums r1, r2;
+          if (item < items) {
+            uint32_t kx, ky, w;
+            item_word(c, item, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, kx, ky, w);
+            Fetched f;
+            fetch_word(c, kx, ky, w, f);
+            update_fetched<FAST, true>(c, f, s_thr, s_alw, stash, &r1, &r2);
+          }
+          add_layer_sums_shared(s_m, s_tot, r1);
+          add_layer_sums_shared(s_m, s_tot, r2);
+        }
+      } else {
+        for (uint32_t item = threadIdx.x; item < items; item += blockDim.x) {
+          uint32_t kx, ky, w;
+          item_word(c, item, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, kx, ky, w);
+          Fetched f;
+          fetch_word(c, kx, ky, w, f);
+          update_fetched<FAST>(c, f, s_thr, s_alw);
+        }
       }
       __syncthreads();
     }
     done = k + 1;
-    if (m_every == 0 || (t + 1) % m_every != 0) continue;
-    // record of sweep t + 1: layer sums in shared memory, bond sum reduced
-    for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) s_m[kx] = 0;
-    __syncthreads();
-    int64_t bsum = 0;
-    const uint32_t total = Lx * Ly * W;
-    for (uint32_t base = 0; base < total; base += blockDim.x) {
-      const uint32_t it = base + threadIdx.x;
-      const bool on = it < total;
-      int m = 0, bb = 0;
-      uint32_t kxm1 = 0xFFFFFFFFu;
-      if (on) {
-        const uint32_t row = it / W, w = it - row * W;
-        kxm1 = row / Ly;
-        measure_word(c.plane0, c.plane1, W, Lx, Ly, W, c.n, c.last_mask, c.x_pbc, c.y_mode, kxm1, row - kxm1 * Ly,
-                     w, m, bb);
-        bsum += bb;
-      }
-      // one atomic per warp when the warp's words share a layer
-      const uint32_t k0 = __shfl_sync(0xFFFFFFFFu, kxm1, 0);
-      if (__all_sync(0xFFFFFFFFu, !on || kxm1 == k0)) {
-        int v = m;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-        if ((threadIdx.x & 31u) == 0 && k0 != 0xFFFFFFFFu) atomicAdd(&s_m[k0], v);
-      } else if (on) {
-        atomicAdd(&s_m[kxm1], m);
-      }
-    }
-    const int64_t tb = block_sum(bsum, s_red);  // its barriers also complete s_m
+    if (!rec_now) continue;
+    // record of sweep t + 1; every thread clears what it read, and the next
+    // sweep's first barrier orders that before the next sums
     const uint32_t slot = s_d.rec_cap ? rec_next % s_d.rec_cap : 0u;
     int64_t* rec = records + s_d.rec_off + (size_t)slot * (5 + Lx);
-    for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) rec[5 + kx] = s_m[kx];
+    for (uint32_t kx = threadIdx.x; kx < Lx; kx += blockDim.x) {
+      const int v = s_m[kx];
+      s_m[kx] = 0;
+      rec[5 + kx] = v;
+      if (kx == 0) rec[3] = v;
+      if (kx == Lx - 1) rec[4] = v;
+    }
     if (threadIdx.x == 0) {
-      int64_t M = 0;
-      for (uint32_t kx = 0; kx < Lx; kx++) M += s_m[kx];
       rec[0] = (int64_t)t + 1;
-      rec[1] = tb;
-      rec[2] = M;
-      rec[3] = s_m[0];
-      rec[4] = s_m[Lx - 1];
+      rec[1] = s_tot[0];
+      rec[2] = s_tot[1];
+      s_tot[0] = 0;
+      s_tot[1] = 0;
     }
     rec_next++;
-    __syncthreads();  // s_m is read above before the next record clears it
   }
   for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
     const uint32_t X = i >= words ? 1u : 0u;
