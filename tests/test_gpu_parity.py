@@ -198,6 +198,34 @@ def test_records_when_measurement_blocks_outnumber_the_grid():
     b.close()
 
 
+@pytest.mark.parametrize("shape", [ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q], ids=["grid1", "grid2", "gridq"])
+def test_records_across_call_boundaries(shape):
+    """Records are summed in half-sweep 1 and written by the next half-sweep 0,
+    except after a call's last sweep (a separate kernel).  Calls of one sweep
+    (every record through the separate kernel), of a few sweeps and of many
+    (graph chunks) alternate on one batch, with records every 1, 2 and 3
+    sweeps and the seam joining one colour or not; records and spins match the
+    oracle."""
+    geoms = [(6, 8, 16), (7, 8, 64), (5, 6, 34), (4, 9, 96), (1, 5, 8), (9, 3, 130)]
+    specs = [dict(Lx=Lx, Ly=Ly, Lz=Lz, T=2.5 + 0.2 * i, H1=0.2 * i - 0.3, seed=77, replica=i, measure_every=1 + i % 3,
+                  init_kind=ig.INIT_SLAB_Y, flip_p=0.05, y_mode=[ig.Y_GAPBC, ig.Y_PBC, ig.Y_APBC][i % 3])
+             for i, (Lx, Ly, Lz) in enumerate(geoms)]
+    calls = [(1, False), (1, True), (3, False), (2, True), (1, False), (70, True), (1, False), (5, False)]
+    b = ig.Batch(specs)
+    b.set_shape(shape)
+    for n, graph in calls:
+        b.sweep(n, graph)
+    total = sum(n for n, _ in calls)
+    for i, sp in enumerate(specs):
+        o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], y_mode=sp["y_mode"],
+                   replica=sp["replica"])
+        o.init(sp["init_kind"], sp["flip_p"])
+        want = o.sweep(total, sp["measure_every"])
+        assert np.array_equal(b.read_series(i), want), i
+        assert np.array_equal(b.get_spins(i), o.get_spins()), i
+    b.close()
+
+
 def test_thermodynamic_integration_from_gpu_records_matches_oracle():
     """The film's own integral over H1 (8 Gauss-Legendre nodes): the FP64 result from the GPU's
     records through the library equals the oracle-fed numpy result to 1e-12."""
