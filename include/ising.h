@@ -218,14 +218,28 @@ typedef struct {
 
 typedef struct ising_batch ising_batch;
 
-/* Allocate and initialise n films updated together: every launch of a
- * batch covers all of its films.  jobs: host array of n.  EINVAL / ENOMEM. */
+#define ISING_MAX_LANES 16
+
+/* Allocate and initialise n films updated together.  The films are spread
+ * over `lanes` lanes (the largest film first, each to the lane with the
+ * fewest sites so far); a lane's launches cover all of its films, and the
+ * lanes run concurrently on their own streams, so that one lane's launch
+ * boundaries overlap another's work.  Every film's chain, records and spins
+ * are the same whatever the lanes.  lanes = 0: two lanes when n >= 2, else
+ * one; more lanes than films are cut to n.  jobs: host array of n.
+ * EINVAL (lanes > ISING_MAX_LANES) / ENOMEM. */
+int ising_batch_create_lanes(const ising_job *jobs, size_t n, uint32_t lanes, ising_batch **out);
+/* ising_batch_create_lanes with lanes = 0. */
 int ising_batch_create(const ising_job *jobs, size_t n, ising_batch **out);
+int ising_batch_get_lanes(const ising_batch *b, uint32_t *lanes);
+/* The batch's stream (lane 0's; NULL: a stream of the library's own).  Each
+ * ising_batch_sweep forks from it to the other lanes and joins back, so work
+ * queued on it after the call sees every film swept. */
 int ising_batch_set_stream(ising_batch *b, void *cuda_stream);
 
 /* Enqueue n_sweeps sweeps of every film (asynchronous).  Records follow each
- * job's measure_every.  use_graph != 0 captures the sweep chunk in a CUDA
- * graph once and replays it. */
+ * job's measure_every.  use_graph != 0 captures each lane's sweep chunk in a
+ * CUDA graph once and replays it. */
 int ising_batch_sweep(ising_batch *b, uint64_t n_sweeps, int use_graph);
 
 /* Room for n_records more pending records of every film that records (see
@@ -239,9 +253,10 @@ int ising_batch_set_shape(ising_batch *b, int shape);
 int ising_batch_get_shape(ising_batch *b, int *shape);
 
 /* Autotuner: times GRID_1, GRID_2 and GRID_Q on a scratch batch of the same jobs
- * (from their initial states; the kernels' work does not depend on the
- * spins), graph replay and records included, and adopts the faster unless
- * a shape is pinned; *shape (may be NULL) receives it.  Synchronises. */
+ * in the same lanes (from their initial states; the kernels' work does not
+ * depend on the spins), all lanes running, graph replay and records
+ * included, and adopts the faster for every lane unless a shape is pinned;
+ * *shape (may be NULL) receives it.  Synchronises. */
 int ising_batch_autotune(ising_batch *b, int *shape);
 
 /* Per-film accessors (index i < n).  Host buffers; synchronise. */
@@ -250,6 +265,7 @@ int ising_batch_read_series(ising_batch *b, size_t i, int64_t *buf, size_t cap, 
 /* Records of film i enqueued so far and not yet read (host counter; does not
  * synchronise). */
 int ising_batch_pending_records(const ising_batch *b, size_t i, size_t *n);
+/* Wait for every lane (bounded by timeout_s; ETIMEOUT otherwise). */
 int ising_batch_synchronize(ising_batch *b, double timeout_s);
 int ising_batch_destroy(ising_batch *b);
 

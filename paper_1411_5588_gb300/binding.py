@@ -21,6 +21,7 @@ Y_GAPBC, Y_PBC, Y_APBC = 0, 1, 2
 X_FREE, X_PBC = 0, 1
 INIT_RANDOM, INIT_SLAB_Y, INIT_ALL_UP = 0, 1, 2
 SHAPE_AUTO, SHAPE_RESIDENT, SHAPE_GRID_1, SHAPE_GRID_2, SHAPE_GRID_Q = 0, 1, 2, 3, 4
+MAX_LANES = 16  # ISING_MAX_LANES
 
 _c = ctypes
 P = _c.c_void_p
@@ -85,6 +86,8 @@ _SIGS = {
     "ising_synchronize": [P, _c.c_double],
     "ising_destroy": [P],
     "ising_batch_create": [_c.POINTER(IsingJob), _c.c_size_t, _c.POINTER(P)],
+    "ising_batch_create_lanes": [_c.POINTER(IsingJob), _c.c_size_t, _c.c_uint32, _c.POINTER(P)],
+    "ising_batch_get_lanes": [P, _c.POINTER(_c.c_uint32)],
     "ising_batch_set_stream": [P, P],
     "ising_batch_sweep": [P, _c.c_uint64, _c.c_int],
     "ising_batch_get_spins": [P, _c.c_size_t, P],
@@ -327,13 +330,15 @@ def make_jobs(specs):
 
 
 class Batch:
-    """Films updated by shared launches (``ising_batch_*``)."""
+    """Films updated by shared launches (``ising_batch_*``), spread over
+    ``lanes`` concurrent lanes (0: the library's default)."""
 
-    def __init__(self, specs, stream=None):
+    def __init__(self, specs, stream=None, lanes=0):
         self.specs = [dict(s) for s in specs]
         self._jobs = make_jobs(self.specs)
         h = P()
-        check(lib().ising_batch_create(self._jobs, len(self.specs), _c.byref(h)), "ising_batch_create")
+        check(lib().ising_batch_create_lanes(self._jobs, len(self.specs), int(lanes), _c.byref(h)),
+              "ising_batch_create_lanes")
         self._h = h
         if stream is not None:
             check(lib().ising_batch_set_stream(h, _torch_stream(stream)), "ising_batch_set_stream")
@@ -347,6 +352,12 @@ class Batch:
 
     def __len__(self):
         return len(self.specs)
+
+    @property
+    def lanes(self):
+        v = _c.c_uint32()
+        check(lib().ising_batch_get_lanes(self._h, _c.byref(v)), "ising_batch_get_lanes")
+        return int(v.value)
 
     def sweep(self, n, use_graph=False):
         check(lib().ising_batch_sweep(self._h, int(n), 1 if use_graph else 0), "ising_batch_sweep")

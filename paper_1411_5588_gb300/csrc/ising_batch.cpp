@@ -1,8 +1,10 @@
 // Static batches: many independent films (different T, H1, shape, key) that
-// share every launch -- the integration points of Eqs. 9, 19 and 22 run as one
-// job.  A chunk of sweeps can be captured once in a CUDA graph and replayed;
-// the films' sweep and record counters live on the device, so the same graph
-// serves every chunk.
+// share launches -- the integration points of Eqs. 9, 19 and 22 run as one
+// job.  The films are spread over lanes, each a film set on its own stream;
+// the lanes run concurrently, so one lane's launch boundaries overlap another
+// lane's work.  A chunk of sweeps can be captured once in a CUDA graph per
+// lane and replayed; the films' sweep and record counters live on the device,
+// so the same graph serves every chunk.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,7 +18,11 @@
 
 using namespace isg;
 
-struct ising_batch {
+namespace {
+
+// One lane of a batch: a film set with its own stream, record rings and
+// captured graphs.  The lanes of a batch run concurrently.
+struct Lane {
   FilmSet fs;
   std::vector<ising_job> jobs;
   std::vector<uint64_t> rec_written, rec_read;
@@ -24,9 +30,8 @@ struct ising_batch {
   int8_t* d_stage = nullptr;
   size_t stage_bytes = 0;
   bool dirty = true;
-  int shape = ISING_SHAPE_AUTO;  // pinned launch shape, or AUTO
-  int tuned_shape = 0;           // ising_batch_autotune's choice (0: none yet)
   std::map<uint32_t, cudaGraphExec_t> graphs;  // chunk length -> executable graph
+  cudaEvent_t ev_done = nullptr;               // the lane's last sweep call has finished
 
   void drop_graphs() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
@@ -34,9 +39,7 @@ struct ising_batch {
   }
 };
 
-namespace {
-
-int batch_sync_desc(ising_batch* b) {
+int lane_sync_desc(Lane* b) {
   if (!b->dirty) return ISING_OK;
   int rc = b->fs.upload();
   if (rc) return rc;
@@ -45,7 +48,7 @@ int batch_sync_desc(ising_batch* b) {
 }
 
 // Make room for `extra[f]` more records of every film (rebuilds the ring area).
-int batch_ensure_rings(ising_batch* b, const std::vector<uint64_t>& extra) {
+int lane_ensure_rings(Lane* b, const std::vector<uint64_t>& extra) {
   FilmSet& fs = b->fs;
   const size_t nf = fs.h.size();
   bool grow = false;
@@ -98,7 +101,7 @@ uint64_t lcm_u64(uint64_t a, uint64_t b) { return a / std::gcd(a, b) * b; }
 
 // Switch the grid kernels' words per thread: new block ranges and owner
 // tables, and the captured graphs (which bake in the old ones) are dropped.
-int apply_items(ising_batch* b, uint32_t items) {
+int lane_apply_items(Lane* b, uint32_t items) {
   if (b->fs.items == items) return ISING_OK;
   ISG_CK(cudaStreamSynchronize(b->fs.stream));
   b->fs.items = items;
@@ -108,7 +111,7 @@ int apply_items(ising_batch* b, uint32_t items) {
   return ISING_OK;
 }
 
-int direct_sweeps(ising_batch* b, uint32_t n) {
+int lane_direct_sweeps(Lane* b, uint32_t n) {
   if (n == 0) return ISING_OK;
   FilmSet& fs = b->fs;
   int rc = fs.enqueue_sweeps(0, n, false, false);
@@ -119,27 +122,16 @@ int direct_sweeps(ising_batch* b, uint32_t n) {
   return ISING_OK;
 }
 
-}  // namespace
+void lane_destroy(Lane* b);
 
-extern "C" {
-
-int ising_batch_create(const ising_job* jobs, size_t n, ising_batch** out) {
-  clear_error();
-  if (!out || (!jobs && n)) return fail(ISING_EINVAL, "NULL argument");
+// A lane of the given films (caller's order within the lane), initial
+// states drawn, descriptors uploaded.
+int lane_create(const std::vector<ising_job>& jobs, Lane** out) {
   *out = nullptr;
-  if (n == 0 || n > (1u << 24)) return fail(ISING_EINVAL, "batch needs 1..2^24 films");
-  for (size_t i = 0; i < n; i++) {
-    const ising_job& j = jobs[i];
-    int rc = check_film(j.Lx, j.Ly, j.Lz, j.T, j.y_mode, j.x_mode);
-    if (rc) return fail(rc, "job %zu: %s", i, ising_last_error());
-    if (j.init_kind < ISING_INIT_RANDOM || j.init_kind > ISING_INIT_ALL_UP)
-      return fail(ISING_EINVAL, "job %zu: bad init kind", i);
-    if (j.init_kind == ISING_INIT_SLAB_Y && !(j.flip_p >= 0.0 && j.flip_p <= 1.0))
-      return fail(ISING_EINVAL, "job %zu: flip_p must be in [0,1]", i);
-  }
-  ising_batch* b = new (std::nothrow) ising_batch();
+  const size_t n = jobs.size();
+  Lane* b = new (std::nothrow) Lane();
   if (!b) return fail(ISING_ENOMEM, "host allocation failed");
-  b->jobs.assign(jobs, jobs + n);
+  b->jobs = jobs;
   b->rec_written.assign(n, 0);
   b->rec_read.assign(n, 0);
   FilmSet& fs = b->fs;
@@ -156,8 +148,16 @@ int ising_batch_create(const ising_job* jobs, size_t n, ising_batch** out) {
     words += (film_words(d) + 63) / 64 * 64;
     stage = std::max(stage, (size_t)j.Lx * j.Ly * j.Lz);
   }
+  auto drop = [&](int rc) {
+    lane_destroy(b);
+    return rc;
+  };
   int rc = fs.init_device();
-  if (rc) { delete b; return rc; }
+  if (rc) return drop(rc);
+  if (cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+    b->ev_done = nullptr;
+    return drop(fail(ISING_ECUDA, "event creation failed"));
+  }
   fs.layout();
   size_t part = 0;
   for (auto& d : fs.h) part += part_len(d);
@@ -165,15 +165,14 @@ int ising_batch_create(const ising_job* jobs, size_t n, ising_batch** out) {
       cudaMalloc(&fs.part, part * sizeof(int64_t)) != cudaSuccess ||
       cudaMemset(fs.part, 0, part * sizeof(int64_t)) != cudaSuccess) {
     cudaGetLastError();
-    ising_batch_destroy(b);
-    return fail(ISING_ENOMEM, "device allocation of %zu words failed", words);
+    return drop(fail(ISING_ENOMEM, "device allocation of %zu words failed", words));
   }
   fs.pool_words = words;
   fs.part_words = part;
   b->stage_bytes = stage;
   std::vector<uint64_t> extra(n, 0);
   for (size_t i = 0; i < n; i++) extra[i] = jobs[i].measure_every ? 64 : 0;
-  rc = batch_ensure_rings(b, extra);
+  rc = lane_ensure_rings(b, extra);
   for (size_t i = 0; !rc && i < n; i++) {
     const ising_job& j = jobs[i];
     uint32_t flip_lo = 0;
@@ -185,34 +184,24 @@ int ising_batch_create(const ising_job* jobs, size_t n, ising_batch** out) {
     if (launch_init(fs.h[i], fs.pool, j.init_kind, flip_lo, flip_all, fs.stream) != cudaSuccess)
       rc = fail(ISING_ECUDA, "init launch failed");
   }
-  if (!rc) rc = batch_sync_desc(b);
-  if (rc) { ising_batch_destroy(b); return rc; }
+  if (!rc) rc = lane_sync_desc(b);
+  if (rc) return drop(rc);
   *out = b;
   return ISING_OK;
 }
 
-int ising_batch_set_stream(ising_batch* b, void* s) {
-  clear_error();
-  if (!b) return fail(ISING_EINVAL, "NULL batch");
-  ISG_CK(cudaStreamSynchronize(b->fs.stream));
-  if (b->fs.own_stream) ISG_CK(cudaStreamDestroy(b->fs.stream));
-  b->fs.own_stream = false;
-  b->fs.stream = nullptr;
-  if (s) {
-    b->fs.stream = (cudaStream_t)s;
-  } else {
-    ISG_CK(cudaStreamCreateWithFlags(&b->fs.stream, cudaStreamNonBlocking));
-    b->fs.own_stream = true;
-  }
+void lane_destroy(Lane* b) {
+  if (!b) return;
+  if (b->fs.stream) cudaStreamSynchronize(b->fs.stream);
   b->drop_graphs();
-  return ISING_OK;
+  if (b->d_stage) cudaFree(b->d_stage);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
+  b->fs.release();
+  delete b;
 }
 
-int ising_batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
-  clear_error();
-  if (!b) return fail(ISING_EINVAL, "NULL batch");
-  if (n == 0) return ISING_OK;
-  if (b->sweeps + n >= 0xFFFFFFFFull) return fail(ISING_EINVAL, "sweep counter would reach 0xFFFFFFFF");
+// n sweeps of every film of the lane, on its stream.
+int lane_sweep(Lane* b, uint64_t n, int use_graph) {
   FilmSet& fs = b->fs;
   const size_t nf = fs.h.size();
   std::vector<uint64_t> extra(nf);
@@ -222,16 +211,16 @@ int ising_batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
     extra[f] = m ? (b->sweeps + n) / m - b->sweeps / m : 0;
     if (m) G = lcm_u64(G, m);
   }
-  int rc = batch_ensure_rings(b, extra);
-  if (!rc) rc = batch_sync_desc(b);
+  int rc = lane_ensure_rings(b, extra);
+  if (!rc) rc = lane_sync_desc(b);
   if (rc) return rc;
   if (G == 1) G = 64;
   while (G < 16) G *= 2;
   if (!use_graph || G > 4096 || n < 2 * G) {
-    rc = direct_sweeps(b, (uint32_t)n);
+    rc = lane_direct_sweeps(b, (uint32_t)n);
   } else {
     const uint64_t prefix = (G - b->sweeps % G) % G;
-    rc = direct_sweeps(b, (uint32_t)prefix);
+    rc = lane_direct_sweeps(b, (uint32_t)prefix);
     uint64_t left = n - prefix;
     const uint32_t g = (uint32_t)G;
     if (!rc && left >= G && !b->graphs.count(g)) {
@@ -255,7 +244,7 @@ int ising_batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
       b->sweeps += g;
       left -= G;
     }
-    if (!rc) rc = direct_sweeps(b, (uint32_t)left);
+    if (!rc) rc = lane_direct_sweeps(b, (uint32_t)left);
   }
   if (rc) return rc;
   for (size_t f = 0; f < nf; f++) {
@@ -265,12 +254,171 @@ int ising_batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
   return ISING_OK;
 }
 
+// Films to lanes: the largest first, each to the lane with the fewest sites
+// so far (the lanes' sweeps take about equally long).
+std::vector<uint32_t> assign_lanes(const ising_job* jobs, size_t n, uint32_t lanes) {
+  std::vector<size_t> order(n);
+  std::iota(order.begin(), order.end(), (size_t)0);
+  auto sites = [&](size_t i) { return (double)jobs[i].Lx * jobs[i].Ly * jobs[i].Lz; };
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return sites(a) > sites(b); });
+  std::vector<double> load(lanes, 0.0);
+  std::vector<uint32_t> lane_of(n);
+  for (size_t i : order) {
+    const uint32_t l = (uint32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+    lane_of[i] = l;
+    load[l] += sites(i);
+  }
+  return lane_of;
+}
+
+}  // namespace
+
+// A batch: its films spread over lanes that sweep concurrently, each on its
+// own stream.  Lane 0's stream is the batch's stream; a sweep forks from it
+// to the other lanes and joins back, so work queued on it afterwards sees
+// every film swept.
+struct ising_batch {
+  std::vector<Lane*> lanes;
+  std::vector<std::pair<uint32_t, uint32_t>> where;  // film -> (lane, index in the lane)
+  std::vector<ising_job> jobs;                        // in the caller's order
+  cudaEvent_t ev_fork = nullptr;
+  int device = 0;
+  int shape = ISING_SHAPE_AUTO;  // pinned launch shape, or AUTO
+  int tuned_shape = 0;           // ising_batch_autotune's choice (0: none yet)
+
+  cudaStream_t stream() const { return lanes[0]->fs.stream; }
+  Lane* lane_of(size_t i) const { return lanes[where[i].first]; }
+  size_t index_in_lane(size_t i) const { return where[i].second; }
+};
+
+namespace {
+
+int batch_apply_items(ising_batch* b, uint32_t items) {
+  for (Lane* l : b->lanes) {
+    int rc = lane_apply_items(l, items);
+    if (rc) return rc;
+  }
+  return ISING_OK;
+}
+
+int batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
+  const size_t nl = b->lanes.size();
+  if (nl > 1) {
+    ISG_CK(cudaEventRecord(b->ev_fork, b->stream()));
+    for (size_t l = 1; l < nl; l++) ISG_CK(cudaStreamWaitEvent(b->lanes[l]->fs.stream, b->ev_fork, 0));
+  }
+  for (Lane* l : b->lanes) {
+    int rc = lane_sweep(l, n, use_graph);
+    if (rc) return rc;
+  }
+  for (size_t l = 1; l < nl; l++) {
+    ISG_CK(cudaEventRecord(b->lanes[l]->ev_done, b->lanes[l]->fs.stream));
+    ISG_CK(cudaStreamWaitEvent(b->stream(), b->lanes[l]->ev_done, 0));
+  }
+  return ISING_OK;
+}
+
+int batch_create(const ising_job* jobs, size_t n, uint32_t lanes, ising_batch** out) {
+  ising_batch* b = new (std::nothrow) ising_batch();
+  if (!b) return fail(ISING_ENOMEM, "host allocation failed");
+  b->jobs.assign(jobs, jobs + n);
+  const std::vector<uint32_t> lane_of = assign_lanes(jobs, n, lanes);
+  std::vector<std::vector<ising_job>> per(lanes);
+  b->where.resize(n);
+  for (size_t i = 0; i < n; i++) {
+    b->where[i] = {lane_of[i], (uint32_t)per[lane_of[i]].size()};
+    per[lane_of[i]].push_back(jobs[i]);
+  }
+  int rc = ISING_OK;
+  for (uint32_t l = 0; !rc && l < lanes; l++) {
+    Lane* ln = nullptr;
+    rc = lane_create(per[l], &ln);
+    if (!rc) b->lanes.push_back(ln);
+  }
+  if (!rc && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    b->ev_fork = nullptr;
+    rc = fail(ISING_ECUDA, "event creation failed");
+  }
+  if (!rc) b->device = b->lanes[0]->fs.device;
+  if (rc) {
+    ising_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ising_batch_create(const ising_job* jobs, size_t n, ising_batch** out) {
+  return ising_batch_create_lanes(jobs, n, 0, out);
+}
+
+int ising_batch_create_lanes(const ising_job* jobs, size_t n, uint32_t lanes, ising_batch** out) {
+  clear_error();
+  if (!out || (!jobs && n)) return fail(ISING_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (n == 0 || n > (1u << 24)) return fail(ISING_EINVAL, "batch needs 1..2^24 films");
+  if (lanes > ISING_MAX_LANES) return fail(ISING_EINVAL, "at most %d lanes", ISING_MAX_LANES);
+  for (size_t i = 0; i < n; i++) {
+    const ising_job& j = jobs[i];
+    int rc = check_film(j.Lx, j.Ly, j.Lz, j.T, j.y_mode, j.x_mode);
+    if (rc) return fail(rc, "job %zu: %s", i, ising_last_error());
+    if (j.init_kind < ISING_INIT_RANDOM || j.init_kind > ISING_INIT_ALL_UP)
+      return fail(ISING_EINVAL, "job %zu: bad init kind", i);
+    if (j.init_kind == ISING_INIT_SLAB_Y && !(j.flip_p >= 0.0 && j.flip_p <= 1.0))
+      return fail(ISING_EINVAL, "job %zu: flip_p must be in [0,1]", i);
+  }
+  if (lanes == 0) lanes = n >= 2 ? 2u : 1u;
+  if (lanes > n) lanes = (uint32_t)n;
+  return batch_create(jobs, n, lanes, out);
+}
+
+int ising_batch_get_lanes(const ising_batch* b, uint32_t* lanes) {
+  clear_error();
+  if (!b || !lanes) return fail(ISING_EINVAL, "NULL argument");
+  *lanes = (uint32_t)b->lanes.size();
+  return ISING_OK;
+}
+
+int ising_batch_set_stream(ising_batch* b, void* s) {
+  clear_error();
+  if (!b) return fail(ISING_EINVAL, "NULL batch");
+  FilmSet& fs = b->lanes[0]->fs;
+  for (Lane* l : b->lanes) ISG_CK(cudaStreamSynchronize(l->fs.stream));
+  if (fs.own_stream) ISG_CK(cudaStreamDestroy(fs.stream));
+  fs.own_stream = false;
+  fs.stream = nullptr;
+  if (s) {
+    fs.stream = (cudaStream_t)s;
+  } else {
+    ISG_CK(cudaStreamCreateWithFlags(&fs.stream, cudaStreamNonBlocking));
+    fs.own_stream = true;
+  }
+  b->lanes[0]->drop_graphs();
+  return ISING_OK;
+}
+
+int ising_batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
+  clear_error();
+  if (!b) return fail(ISING_EINVAL, "NULL batch");
+  if (n == 0) return ISING_OK;
+  if (b->lanes[0]->sweeps + n >= 0xFFFFFFFFull) return fail(ISING_EINVAL, "sweep counter would reach 0xFFFFFFFF");
+  return batch_sweep(b, n, use_graph);
+}
+
 int ising_batch_reserve_records(ising_batch* b, uint64_t n_records) {
   clear_error();
   if (!b) return fail(ISING_EINVAL, "NULL batch");
-  std::vector<uint64_t> extra(b->fs.h.size());
-  for (size_t f = 0; f < extra.size(); f++) extra[f] = b->fs.h[f].measure_every ? n_records : 0;
-  return batch_ensure_rings(b, extra);
+  for (Lane* l : b->lanes) {
+    std::vector<uint64_t> extra(l->fs.h.size());
+    for (size_t f = 0; f < extra.size(); f++) extra[f] = l->fs.h[f].measure_every ? n_records : 0;
+    int rc = lane_ensure_rings(l, extra);
+    if (rc) return rc;
+  }
+  return ISING_OK;
 }
 
 int ising_batch_set_shape(ising_batch* b, int shape) {
@@ -282,27 +430,28 @@ int ising_batch_set_shape(ising_batch* b, int shape) {
   b->shape = shape;
   const uint32_t items = shape == ISING_SHAPE_AUTO ? (b->tuned_shape ? shape_items(b->tuned_shape) : 1u)
                                                    : shape_items(shape);
-  return apply_items(b, items);
+  return batch_apply_items(b, items);
 }
 
 int ising_batch_get_shape(ising_batch* b, int* shape) {
   clear_error();
   if (!b || !shape) return fail(ISING_EINVAL, "NULL argument");
-  *shape = items_shape(b->fs.items);
+  *shape = items_shape(b->lanes[0]->fs.items);
   return ISING_OK;
 }
 
 int ising_batch_autotune(ising_batch* b, int* shape) {
   clear_error();
   if (!b) return fail(ISING_EINVAL, "NULL batch");
-  // a scratch batch of the same films from their initial states: the kernels
-  // do the same work whatever the spins are, and this batch is not touched
-  DeviceGuard dev(b->fs.device);
+  // a scratch batch of the same films in the same lanes, from their initial
+  // states: the kernels do the same work whatever the spins are, and this
+  // batch is not touched; every candidate is timed with all lanes running
+  DeviceGuard dev(b->device);
   ising_batch* s = nullptr;
-  int rc = ising_batch_create(b->jobs.data(), b->jobs.size(), &s);
+  int rc = ising_batch_create_lanes(b->jobs.data(), b->jobs.size(), (uint32_t)b->lanes.size(), &s);
   if (rc) return rc;
   double sites = 0;
-  for (const auto& d : b->fs.h) sites += (double)d.Lx * d.Ly * d.Lz;
+  for (const auto& j : b->jobs) sites += (double)j.Lx * j.Ly * j.Lz;
   const uint64_t n = (uint64_t)std::min(1024.0, std::max(64.0, std::round(4e8 / sites)));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -310,17 +459,18 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   int best = ISING_SHAPE_GRID_1;
   float best_ms = 3.0e38f;
   for (int cand = ISING_SHAPE_GRID_1; !rc && cand <= ISING_SHAPE_GRID_Q; cand++) {
-    rc = apply_items(s, shape_items(cand));
+    rc = batch_apply_items(s, shape_items(cand));
     float ms = 3.0e38f;
-    for (int rep = 0; !rc && rep < 3; rep++) {  // the first run captures the graph
-      if (cudaEventRecord(e0, s->fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
-      if (!rc) rc = ising_batch_sweep(s, n, 1);
-      if (!rc && cudaEventRecord(e1, s->fs.stream) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
+    for (int rep = 0; !rc && rep < 3; rep++) {  // the first run captures the graphs
+      if (cudaEventRecord(e0, s->stream()) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
+      if (!rc) rc = batch_sweep(s, n, 1);
+      if (!rc && cudaEventRecord(e1, s->stream()) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
       if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ISING_ECUDA, "event wait failed");
       float t = 0.f;
       if (!rc && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = fail(ISING_ECUDA, "event time failed");
       if (!rc && rep > 0) ms = std::min(ms, t);
-      for (size_t f = 0; f < s->fs.h.size(); f++) s->rec_read[f] = s->rec_written[f];  // drop the records
+      for (Lane* l : s->lanes)  // drop the records
+        for (size_t f = 0; f < l->fs.h.size(); f++) l->rec_read[f] = l->rec_written[f];
     }
     if (!rc && ms < kTuneMargin * best_ms) {  // a later shape must win clearly
       best_ms = ms;
@@ -332,7 +482,7 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   ising_batch_destroy(s);
   if (rc) return rc;
   b->tuned_shape = best;
-  if (b->shape == ISING_SHAPE_AUTO) rc = apply_items(b, shape_items(best));
+  if (b->shape == ISING_SHAPE_AUTO) rc = batch_apply_items(b, shape_items(best));
   if (!rc && shape) *shape = best;
   return rc;
 }
@@ -340,34 +490,37 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
 int ising_batch_get_spins(ising_batch* b, size_t i, int8_t* s) {
   clear_error();
   if (!b || !s) return fail(ISING_EINVAL, "NULL argument");
-  if (i >= b->fs.h.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
-  if (!b->d_stage) ISG_CK(cudaMalloc(&b->d_stage, b->stage_bytes));
-  const FilmDesc& d = b->fs.h[i];
-  ISG_CK(launch_unpack(d, b->fs.pool, b->d_stage, b->fs.stream));
-  ISG_CK(cudaMemcpyAsync(s, b->d_stage, (size_t)d.Lx * d.Ly * d.Lz, cudaMemcpyDeviceToHost, b->fs.stream));
-  ISG_CK(cudaStreamSynchronize(b->fs.stream));
+  if (i >= b->jobs.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
+  Lane* l = b->lane_of(i);
+  if (!l->d_stage) ISG_CK(cudaMalloc(&l->d_stage, l->stage_bytes));
+  const FilmDesc& d = l->fs.h[b->index_in_lane(i)];
+  ISG_CK(launch_unpack(d, l->fs.pool, l->d_stage, l->fs.stream));
+  ISG_CK(cudaMemcpyAsync(s, l->d_stage, (size_t)d.Lx * d.Ly * d.Lz, cudaMemcpyDeviceToHost, l->fs.stream));
+  ISG_CK(cudaStreamSynchronize(l->fs.stream));
   return ISING_OK;
 }
 
 int ising_batch_read_series(ising_batch* b, size_t i, int64_t* buf, size_t cap, size_t* n_records) {
   clear_error();
   if (!b || !n_records || (cap && !buf)) return fail(ISING_EINVAL, "NULL argument");
-  if (i >= b->fs.h.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
-  ISG_CK(cudaStreamSynchronize(b->fs.stream));
-  const FilmDesc& d = b->fs.h[i];
+  if (i >= b->jobs.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
+  Lane* l = b->lane_of(i);
+  const size_t j = b->index_in_lane(i);
+  ISG_CK(cudaStreamSynchronize(l->fs.stream));
+  const FilmDesc& d = l->fs.h[j];
   const size_t rl = record_len(d);
-  const uint64_t pending = b->rec_written[i] - b->rec_read[i];
+  const uint64_t pending = l->rec_written[j] - l->rec_read[j];
   const uint64_t k = std::min<uint64_t>(pending, cap);
   uint64_t t = 0;
   while (t < k) {
-    const uint64_t slot = (b->rec_read[i] + t) % d.rec_cap;
+    const uint64_t slot = (l->rec_read[j] + t) % d.rec_cap;
     const uint64_t run = std::min<uint64_t>(k - t, d.rec_cap - slot);
-    ISG_CK(cudaMemcpyAsync(buf + t * rl, b->fs.rec + d.rec_off + slot * rl, run * rl * sizeof(int64_t),
-                           cudaMemcpyDeviceToHost, b->fs.stream));
+    ISG_CK(cudaMemcpyAsync(buf + t * rl, l->fs.rec + d.rec_off + slot * rl, run * rl * sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, l->fs.stream));
     t += run;
   }
-  ISG_CK(cudaStreamSynchronize(b->fs.stream));
-  b->rec_read[i] += k;
+  ISG_CK(cudaStreamSynchronize(l->fs.stream));
+  l->rec_read[j] += k;
   *n_records = (size_t)k;
   return ISING_OK;
 }
@@ -375,23 +528,27 @@ int ising_batch_read_series(ising_batch* b, size_t i, int64_t* buf, size_t cap, 
 int ising_batch_pending_records(const ising_batch* b, size_t i, size_t* n) {
   clear_error();
   if (!b || !n) return fail(ISING_EINVAL, "NULL argument");
-  if (i >= b->fs.h.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
-  *n = (size_t)(b->rec_written[i] - b->rec_read[i]);
+  if (i >= b->jobs.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
+  const Lane* l = b->lane_of(i);
+  const size_t j = b->index_in_lane(i);
+  *n = (size_t)(l->rec_written[j] - l->rec_read[j]);
   return ISING_OK;
 }
 
 int ising_batch_synchronize(ising_batch* b, double timeout_s) {
   clear_error();
   if (!b) return fail(ISING_EINVAL, "NULL batch");
-  return wait_stream(b->fs.stream, timeout_s);
+  for (Lane* l : b->lanes) {  // the batch's stream has joined the others; wait on each all the same
+    int rc = wait_stream(l->fs.stream, timeout_s);
+    if (rc) return rc;
+  }
+  return ISING_OK;
 }
 
 int ising_batch_destroy(ising_batch* b) {
   if (!b) return ISING_OK;
-  if (b->fs.stream) cudaStreamSynchronize(b->fs.stream);
-  b->drop_graphs();
-  if (b->d_stage) cudaFree(b->d_stage);
-  b->fs.release();
+  for (Lane* l : b->lanes) lane_destroy(l);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   delete b;
   return ISING_OK;
 }

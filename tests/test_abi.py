@@ -73,3 +73,12 @@ def test_invalid_sizes_are_rejected_before_any_device_call():
     with pytest.raises(ig.IsingError) as e:
         ig.Film(4, 4, 4, 1.0, 0.0, -1.0, 1)
     assert e.value.status == ig.EINVAL
+
+
+def test_batch_lanes_above_the_limit_are_einval():
+    """Checked before any device work, so it runs without a GPU."""
+    import paper_1411_5588_gb300 as ig
+    spec = dict(Lx=4, Ly=4, Lz=8, T=3.0, H1=0.1, seed=1, replica=0)
+    with pytest.raises(ig.IsingError) as e:
+        ig.Batch([spec], lanes=ig.MAX_LANES + 1)
+    assert e.value.status == ig.EINVAL

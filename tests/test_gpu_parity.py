@@ -341,3 +341,48 @@ def test_async_record_reads_match_the_oracle():
         assert np.array_equal(rest, want[10:])
         assert np.array_equal(g.get_spins(), o.get_spins())
         g.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 3, 5])
+def test_lanes_give_the_same_chains(lanes):
+    """However the films are spread over lanes, every film's records and spins
+    are the oracle's (direct and graph calls, records every 1-3 sweeps, a
+    shape pinned and the autotuner's)."""
+    geoms = [(6, 8, 16), (12, 20, 64), (5, 6, 34), (4, 9, 96), (1, 5, 8), (9, 3, 130), (16, 12, 96)]
+    specs = [dict(Lx=Lx, Ly=Ly, Lz=Lz, T=2.2 + 0.3 * i, H1=0.1 * i, seed=31, replica=i, measure_every=1 + i % 3,
+                  init_kind=ig.INIT_RANDOM if i % 2 else ig.INIT_SLAB_Y, flip_p=0.02,
+                  y_mode=[ig.Y_GAPBC, ig.Y_PBC, ig.Y_APBC][i % 3]) for i, (Lx, Ly, Lz) in enumerate(geoms)]
+    b = ig.Batch(specs, lanes=lanes)
+    assert b.lanes == min(lanes, len(specs))
+    b.set_shape(ig.SHAPE_GRID_2)
+    b.sweep(7, False)
+    b.autotune()
+    b.sweep(100, True)
+    for i, sp in enumerate(specs):
+        o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], y_mode=sp["y_mode"],
+                   replica=sp["replica"])
+        o.init(sp["init_kind"], sp["flip_p"])
+        want = o.sweep(107, sp["measure_every"])
+        assert np.array_equal(b.read_series(i), want), i
+        assert np.array_equal(b.get_spins(i), o.get_spins()), i
+    b.close()
+
+
+def test_lanes_join_the_batch_stream():
+    """Work queued on the batch's stream after a sweep sees every lane's
+    films swept: a torch copy of a lane-1 film's spins taken on that stream
+    right after the sweep call matches the final lattice."""
+    torch = pytest.importorskip("torch")
+    specs = [dict(Lx=8, Ly=10, Lz=64, T=3.0, H1=0.2, seed=5, replica=i, measure_every=0) for i in range(4)]
+    st = torch.cuda.Stream()
+    b = ig.Batch(specs, stream=st, lanes=2)
+    b.sweep(40, True)
+    done = torch.cuda.Event()
+    done.record(st)
+    done.synchronize()
+    for i, sp in enumerate(specs):
+        o = O.Film(8, 10, 64, 1.0, 0.2, 3.0, 5, replica=i)
+        o.init(O.INIT_RANDOM)
+        o.sweep(40, 0)
+        assert np.array_equal(b.get_spins(i), o.get_spins()), i
+    b.close()
