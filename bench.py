@@ -231,6 +231,7 @@ def batched_vs_plain(ig, WL, torch, sweeps=20):
     b.sweep(2 * sweeps, True)
     b.synchronize()
     tb = time.perf_counter() - t0
+    lanes = b.lanes
     b.close()
     batched = per_sweep * 2 * sweeps / tb / 1e9
     tp = 0.0
@@ -248,6 +249,7 @@ def batched_vs_plain(ig, WL, torch, sweeps=20):
     plain = per_sweep * sweeps / tp / 1e9
     return {"workload": "64 films 32x64x128..96x192x384 (16 H1 nodes x 2 T x 2 seeds), records every 10 sweeps",
             "batched": batched, "plain": plain, "ratio": batched / plain, "unit": UNIT, "batched_shape": shape,
+            "batched_lanes": lanes,
             "batched_alu_frac": alu_frac(batched),
             "note": "both sides autotuned (library autotuner) before timing",
             "sweeps": {"batched": 2 * sweeps, "plain_per_film": sweeps}}
@@ -332,21 +334,24 @@ def film_8_run(ig, WL):
     return out
 
 
-def t_scan_slice(ig, WL, sweeps=4):
-    """The 40-film temperature scan (40 x 120x240x1600), a few sweeps with a
-    record after every sweep."""
-    jobs = WL.t_scan_40(n_sweeps=sweeps)
+def t_scan_slice(ig, WL, sweeps=10):
+    """The 40-film temperature scan (40 x 120x240x1600) as one autotuned
+    batch, a few sweeps with a record after every sweep."""
+    jobs = WL.t_scan_40(n_sweeps=sweeps + 1)
     b = ig.Batch(jobs)
+    shape = SHAPE_NAMES[b.autotune()]
+    b.reserve_records(sweeps + 1)
     b.sweep(1)
     b.synchronize()
     t0 = time.perf_counter()
     b.sweep(sweeps)
     b.synchronize()
     dt = time.perf_counter() - t0
+    lanes = b.lanes
     b.close()
     a = sum(WL.sites(j) for j in jobs) * sweeps / dt / 1e9
     return {"workload": f"40 films 120x240x1600 (T = 1.5..4.4), {sweeps} sweeps with a record every sweep",
-            "attempts_per_ns": a, "alu_frac": alu_frac(a), "wall_s": dt}
+            "attempts_per_ns": a, "alu_frac": alu_frac(a), "wall_s": dt, "shape": shape, "lanes": lanes}
 
 
 def procedures(ig, WL):
@@ -370,10 +375,11 @@ def procedures(ig, WL):
         b.synchronize()
         dt = time.perf_counter() - t0
         recs = [b.read_series(i) for i in range(len(wl["jobs"]))]
+        lanes = b.lanes
         b.close()
         att = sum(WL.sites(j) for j in wl["jobs"]) * wl["n_sweeps"]
         return recs, {"films": len(wl["jobs"]), "attempts": att, "sweep_s": dt, "attempts_per_ns": att / dt / 1e9,
-                      "alu_frac": alu_frac(att / dt / 1e9), "shape": shape}
+                      "alu_frac": alu_frac(att / dt / 1e9), "shape": shape, "lanes": lanes}
 
     out = {}
     it = WL.interface_tension_set()
