@@ -236,9 +236,10 @@ __device__ __noinline__ void write_record(FilmDesc* Fg, const FilmDesc& F, uint3
 //   sum_d popc(a'_d) = n_old + D popc(fl) - 2 n_fl,
 // n_old and n_fl being the aligned counts summed over the valid and over the
 // flipped sites.  decide_word parks c0, c1, c2 and the row's other word z0 in
-// the thread's kStashSlots consecutive shared-memory words (thread-major; the
-// odd stride keeps a warp's accesses on distinct banks) across the Philox
-// draws, so the sums cost no registers there.
+// slots 0-3 of the thread's kStashSlots consecutive shared-memory words
+// (thread-major; the odd stride keeps a warp's accesses on distinct banks)
+// across the Philox draws, so the sums cost no registers there; slot 4 holds
+// a partner word's seam adjustment across its draws.
 constexpr uint32_t kStashSlots = 5;
 
 struct LayerSums {
