@@ -2,10 +2,11 @@
 64-film integration set (16 H1 nodes x 2 T x 2 seeds, Lx 32..96) or one of
 the procedure sets at the paper's sizes (contact angle, beta integration,
 line tension), records after every sweep unless --every says otherwise
-(0: none).  The command the batch kernels' ncu summaries in profiles/ were
-captured from.
+(0: none), in one lane unless --lanes says otherwise (so that one launch
+covers the whole set).  The command the batch kernels' ncu summaries in
+profiles/ were captured from.
 
-    python -m paper_1411_5588_gb300.profile_batch [--set ti64] [--shape grid2] [--sweeps 4] [--every N]
+    python -m paper_1411_5588_gb300.profile_batch [--set ti64] [--shape grid2] [--sweeps 4] [--every N] [--lanes L]
 """
 from __future__ import annotations
 
@@ -29,18 +30,20 @@ def main():
     ap.add_argument("--shape", default="grid2", choices=sorted(SHAPES))
     ap.add_argument("--sweeps", type=int, default=4)
     ap.add_argument("--every", type=int, default=None, help="record interval (0: no records)")
+    ap.add_argument("--lanes", type=int, default=1, help="batch lanes (0: the library's default)")
     args = ap.parse_args()
     jobs = SETS[args.set](args.sweeps)
     if args.every is not None:
         jobs = [dict(j, measure_every=args.every) for j in jobs]
-    b = ig.Batch(jobs)
+    b = ig.Batch(jobs, lanes=args.lanes)
     b.set_shape(SHAPES[args.shape])
     if args.every != 0:
         b.reserve_records(args.sweeps)
     b.sweep(args.sweeps, False)
     b.synchronize()
+    lanes = b.lanes
     b.close()
-    print(f"{args.set}: {len(jobs)} films, {args.sweeps} sweeps, shape {args.shape}, "
+    print(f"{args.set}: {len(jobs)} films in {lanes} lane(s), {args.sweeps} sweeps, shape {args.shape}, "
           f"records every {jobs[0]['measure_every']} sweeps")
 
 
