@@ -74,3 +74,37 @@ def test_random_batch(seed):
         assert np.array_equal(b.read_series(i), want), sp
         assert np.array_equal(b.get_spins(i), o.get_spins()), sp
     b.close()
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_random_batch_chains(seed):
+    """Random films in a random number of lanes, driven by a random sequence
+    of calls: short and long sweeps, direct and graph, records every 0-4
+    sweeps, the launch shape switched between calls, records read part-way.
+    Every film's records and final spins are the oracle's."""
+    rng = np.random.default_rng(seed)
+    films = _films(seed, 16)
+    specs = [dict(f, measure_every=int(rng.integers(0, 5))) for f in films]
+    lanes = int(rng.integers(1, 5))
+    b = ig.Batch(specs, lanes=lanes)
+    assert b.lanes == min(lanes, len(specs))
+    shapes = [ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q]
+    oracles = [_oracle(sp) for sp in specs]
+    got = [[] for _ in specs]
+    want = [[] for _ in specs]
+    for _ in range(6):
+        b.set_shape(shapes[int(rng.integers(0, 3))])
+        n = int(rng.choice([1, 2, 5, 33, 70]))
+        b.sweep(n, bool(rng.integers(0, 2)))
+        for i, sp in enumerate(specs):
+            want[i].append(oracles[i].sweep(n, sp["measure_every"]))
+        if rng.random() < 0.5:  # read everything pending so far
+            for i in range(len(specs)):
+                got[i].append(b.read_series(i))
+    for i, sp in enumerate(specs):
+        got[i].append(b.read_series(i))
+        g = np.concatenate(got[i]) if got[i] else np.zeros((0, 5 + sp["Lx"]), dtype=np.int64)
+        w = np.concatenate(want[i])
+        assert np.array_equal(g, w), (seed, i, sp)
+        assert np.array_equal(b.get_spins(i), oracles[i].get_spins()), (seed, i, sp)
+    b.close()
