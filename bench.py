@@ -549,7 +549,9 @@ def main():
     film.close()
     if rank != 0:
         return
-    per_step_launches = 2 * SWEEPS_PER_STEP + 2 + 1
+    # per step: two half-sweep launches per sweep (the last one of the step
+    # also takes the record sums), record_kernel, and the sweep-counter advance
+    per_step_launches = 2 * SWEEPS_PER_STEP + 1 + 1
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
