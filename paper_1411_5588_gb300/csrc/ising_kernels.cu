@@ -631,7 +631,10 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // no film of the launch has a reachable thr = 0 entry (the compare-only
 // table); otherwise every film takes the exact variant (which, at two words
 // per thread, needs the registers of one block per SM fewer, and so does its
-// recording form at one word).  MODE kUpdAccumulate: the half-sweep 1 launch
+// recording form at one word).  At one word per thread the plain and
+// record-writing forms fit one block per SM more (kMultiMinBlocks1), so that a
+// small film set's half-sweep is one wave where it would spill into a second.
+// MODE kUpdAccumulate: the half-sweep 1 launch
 // of a sweep after which some film records; those films add their record
 // sums into their accumulators in `part`.  MODE kUpdWriteRecord: a half-sweep
 // 0 launch right after such a sweep; the first block of each film that
@@ -640,7 +643,8 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 enum : uint32_t { kUpdPlain = 0, kUpdAccumulate = 1, kUpdWriteRecord = 2 };
 
 template <bool FAST, uint32_t ITEMS, uint32_t MODE>
-__global__ void __launch_bounds__(kFilmThreads, (FAST || (ITEMS < 2 && MODE != kUpdAccumulate))
+__global__ void __launch_bounds__(kFilmThreads, (ITEMS == 1 && MODE != kUpdAccumulate) ? kMultiMinBlocks1
+                                                : (FAST || (ITEMS < 2 && MODE != kUpdAccumulate))
                                                     ? kMultiMinBlocks : kMultiMinBlocks - 1)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
               const LaunchHdr* __restrict__ hdr, uint32_t* __restrict__ pool, uint32_t colour, uint32_t k,

@@ -17,6 +17,7 @@ namespace isg {
 constexpr uint32_t kFilmThreads = 128;
 constexpr int kFilmMinBlocks = 6;
 constexpr int kMultiMinBlocks = 6;
+constexpr int kMultiMinBlocks1 = 7;  // multi-film kernel, one word per thread, not summing records
 // items = 0 is the quarter shape: four lanes share each word (they split its
 // eight Philox calls), so a block covers kFilmThreads / 4 words.
 __host__ __device__ constexpr uint32_t words_per_block(uint32_t items) {
