@@ -8,10 +8,12 @@
 //      final spins out of pinned staging, return their arena space;
 //   2. admit queued jobs, in arrival order, while their packed lattice, record
 //      series, partial sums and unpack staging fit in a fixed device arena;
-//   3. write the descriptors of the running jobs into the slot's pinned
-//      staging, copy them to the slot's device buffer, enqueue the chunk's
-//      update/measure launches over all of them and an advance of their sweep
-//      counters, and queue the unpack + copy-out of the jobs that finish
+//   3. split the running jobs between two lanes (by sites), write each
+//      lane's descriptors into the slot's pinned staging and copy them to the
+//      slot's device buffer, enqueue each lane's update/record launches and
+//      the advance of its sweep counters on the lane's own stream (the lanes
+//      run concurrently: one's launch boundaries overlap the other's work),
+//      join them, and queue the unpack + copy-out of the jobs that finish
 //      inside the chunk.
 // The host prepares chunk i+1 while chunk i runs.
 // A job that reaches its last sweep inside a chunk stops there (sweep_end).
@@ -25,6 +27,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -113,10 +116,10 @@ size_t footprint_bytes(const Job& j) { return j.b_spin + j.b_rec + j.b_part + j.
 // One of the two chunk slots: device descriptors, pinned staging for them, the
 // event that marks the chunk done, and pinned space for finished results.
 struct Slot {
-  char* d_meta = nullptr;
+  char* d_meta = nullptr;   // [lane 0 | lane 1], meta_bytes each
   char* h_stage = nullptr;
   cudaEvent_t done = nullptr;
-  LaunchSet L;
+  LaunchSet L, L2;          // lane 0, lane 1
   bool busy = false;
   std::vector<ising_ticket> finishing;
   std::vector<size_t> res_off;
@@ -137,7 +140,9 @@ struct ising_server {
   uint32_t chunk = 100;
   char* arena_dev = nullptr;
   Arena arena;
-  FilmSet fs;  // device, stream, occupancy; pool/part/rec point into the arena
+  FilmSet fs;   // lane 0: device, stream, occupancy; pool/part/rec point into the arena
+  FilmSet fs2;  // lane 1: its own stream, the same arena
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::deque<ising_ticket> queue;
   std::unordered_map<ising_ticket, Job> jobs;
   std::vector<ising_ticket> running;
@@ -148,7 +153,7 @@ struct ising_server {
   // chunk slots and the capacities their descriptor buffers were sized for
   Slot slot[2];
   uint32_t cap_films = 0, cap_upd = 0, cap_meas = 0;
-  size_t meta_bytes = 0;
+  size_t meta_bytes = 0;  // one lane's share of a slot's descriptor buffer
   uint32_t grid_upd = 0, grid_meas = 0, grid_fin = 0, grid_adv = 0;
 
   double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -157,6 +162,7 @@ struct ising_server {
   int wait_slot(Slot& s);
   void retire(Slot& s);  // with the lock held
   void release_slots();
+  void release_lanes();  // both film sets, the fork/join events and the arena
 };
 
 // Descriptor buffers large enough for nf films, nu update and nm measurement
@@ -175,17 +181,22 @@ int ising_server::ensure_capacity(uint32_t nf, uint32_t nu, uint32_t nm) {
   cap_upd = grow(cap_upd, nu, 1u << 16);
   cap_meas = grow(cap_meas, nm, 1u << 16);
   meta_bytes = sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc) + ((size_t)cap_upd + cap_meas) * 4;
+  meta_bytes = (meta_bytes + kAlign - 1) / kAlign * kAlign;
+  auto carve = [&](char* base, LaunchSet& L) {
+    L.hdr = reinterpret_cast<LaunchHdr*>(base);
+    L.films = reinterpret_cast<FilmDesc*>(base + sizeof(LaunchHdr));
+    L.owner_upd = reinterpret_cast<uint32_t*>(base + sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc));
+    L.owner_meas = L.owner_upd + cap_upd;
+  };
   for (Slot& s : slot) {
     if (s.d_meta) cudaFree(s.d_meta);
     if (s.h_stage) cudaFreeHost(s.h_stage);
     s.d_meta = nullptr;
     s.h_stage = nullptr;
-    ISG_CK(cudaMalloc(&s.d_meta, meta_bytes));
-    ISG_CK(cudaMallocHost(&s.h_stage, meta_bytes));
-    s.L.hdr = reinterpret_cast<LaunchHdr*>(s.d_meta);
-    s.L.films = reinterpret_cast<FilmDesc*>(s.d_meta + sizeof(LaunchHdr));
-    s.L.owner_upd = reinterpret_cast<uint32_t*>(s.d_meta + sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc));
-    s.L.owner_meas = s.L.owner_upd + cap_upd;
+    ISG_CK(cudaMalloc(&s.d_meta, 2 * meta_bytes));
+    ISG_CK(cudaMallocHost(&s.h_stage, 2 * meta_bytes));
+    carve(s.d_meta, s.L);
+    carve(s.d_meta + meta_bytes, s.L2);
   }
   return ISING_OK;
 }
@@ -288,12 +299,24 @@ void ising_server::loop() {
       cv_work.wait_for(lk, std::chrono::milliseconds(2));
       continue;
     }
-    // descriptors, owner tables and the jobs finishing in this chunk
+    // descriptors of the two lanes (the largest job first, each to the lane
+    // with the fewer sites so far), and the jobs finishing in this chunk
     fs.h.clear();
+    fs2.h.clear();
     std::vector<Job*> fresh, fin;
+    {
+      std::vector<ising_ticket> order(films);
+      auto sites = [&](ising_ticket t) { return (double)jobs[t].d.Lx * jobs[t].d.Ly * jobs[t].d.Lz; };
+      std::stable_sort(order.begin(), order.end(), [&](ising_ticket a, ising_ticket b) { return sites(a) > sites(b); });
+      double load0 = 0, load1 = 0;
+      for (ising_ticket t : order) {
+        const bool first = load0 <= load1;
+        (first ? fs.h : fs2.h).push_back(jobs[t].d);
+        (first ? load0 : load1) += sites(t);
+      }
+    }
     for (ising_ticket t : films) {
       Job& j = jobs[t];
-      fs.h.push_back(j.d);
       if (!j.inited) fresh.push_back(&j);
       if (j.d.sweep_end - j.d.sweep <= chunk) fin.push_back(&j);
     }
@@ -301,20 +324,40 @@ void ising_server::loop() {
     for (ising_ticket t : films)
       if (jobs[t].d.sweep_end - jobs[t].d.sweep <= chunk) S.finishing.push_back(t);
     lk.unlock();
+    fs2.items = fs.items;
     fs.layout(false);  // partial sums stay in each job's own arena area
-    int rc = ensure_capacity(fs.hh.n_films, fs.hh.upd_blocks, fs.hh.meas_blocks);
-    if (!rc) {
-      char* p = S.h_stage;
-      std::memcpy(p, &fs.hh, sizeof fs.hh);
-      std::memcpy(p + sizeof(LaunchHdr), fs.h.data(), fs.h.size() * sizeof(FilmDesc));
+    fs2.layout(false);
+    int rc = ensure_capacity(std::max(fs.hh.n_films, fs2.hh.n_films), std::max(fs.hh.upd_blocks, fs2.hh.upd_blocks),
+                             std::max(fs.hh.meas_blocks, fs2.hh.meas_blocks));
+    // [hdr | films | owner_upd | owner_meas] of one lane into pinned staging
+    auto stage = [&](const FilmSet& F, char* p) {
+      std::memcpy(p, &F.hh, sizeof F.hh);
+      std::memcpy(p + sizeof(LaunchHdr), F.h.data(), F.h.size() * sizeof(FilmDesc));
       uint32_t* ou = reinterpret_cast<uint32_t*>(p + sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc));
       uint32_t* om = ou + cap_upd;
-      for (size_t f = 0; f < fs.h.size(); f++) {
-        const FilmDesc& d = fs.h[f];
-        const uint32_t nb = (d.upd_items + words_per_block(fs.items) - 1) / words_per_block(fs.items);
+      for (size_t f = 0; f < F.h.size(); f++) {
+        const FilmDesc& d = F.h[f];
+        const uint32_t nb = (d.upd_items + words_per_block(F.items) - 1) / words_per_block(F.items);
         for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
         for (uint32_t b = 0; b < meas_units(d); b++) om[d.meas_block_begin + b] = (uint32_t)f;
       }
+    };
+    // the used parts of one lane's buffer, on lane 0's stream
+    auto upload = [&](const FilmSet& F, char* dev, const char* host) {
+      const size_t off_u = sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc);
+      const size_t off_m = off_u + (size_t)cap_upd * 4;
+      const size_t b0 = sizeof(LaunchHdr) + F.h.size() * sizeof(FilmDesc);
+      if (cudaMemcpyAsync(dev, host, b0, cudaMemcpyHostToDevice, fs.stream) != cudaSuccess ||
+          cudaMemcpyAsync(dev + off_u, host + off_u, (size_t)F.hh.upd_blocks * 4, cudaMemcpyHostToDevice,
+                          fs.stream) != cudaSuccess ||
+          cudaMemcpyAsync(dev + off_m, host + off_m, (size_t)F.hh.meas_blocks * 4, cudaMemcpyHostToDevice,
+                          fs.stream) != cudaSuccess)
+        return fail(ISING_ECUDA, "descriptor upload failed");
+      return (int)ISING_OK;
+    };
+    if (!rc) {
+      stage(fs, S.h_stage);
+      if (!fs2.h.empty()) stage(fs2, S.h_stage + meta_bytes);
       // pinned space for the results of the jobs finishing in this chunk
       size_t need = 0;
       S.res_off.clear();
@@ -349,22 +392,29 @@ void ising_server::loop() {
       if (launch_init(j->d, fs.pool, j->p.init_kind, flip_lo, flip_all, fs.stream) != cudaSuccess)
         rc = fail(ISING_ECUDA, "init launch failed");
     }
-    if (!rc) {  // the used parts of [hdr | films | owner_upd | owner_meas]
-      const size_t off_u = sizeof(LaunchHdr) + (size_t)cap_films * sizeof(FilmDesc);
-      const size_t off_m = off_u + (size_t)cap_upd * 4;
-      const size_t b0 = sizeof(LaunchHdr) + fs.h.size() * sizeof(FilmDesc);
-      if (cudaMemcpyAsync(S.d_meta, S.h_stage, b0, cudaMemcpyHostToDevice, fs.stream) != cudaSuccess ||
-          cudaMemcpyAsync(S.d_meta + off_u, S.h_stage + off_u, (size_t)fs.hh.upd_blocks * 4,
-                          cudaMemcpyHostToDevice, fs.stream) != cudaSuccess ||
-          cudaMemcpyAsync(S.d_meta + off_m, S.h_stage + off_m, (size_t)fs.hh.meas_blocks * 4,
-                          cudaMemcpyHostToDevice, fs.stream) != cudaSuccess)
-        rc = fail(ISING_ECUDA, "descriptor upload failed");
-    }
-    if (!rc) {  // the chunk: exact grids, records only after sweeps where some job takes one
+    if (!rc) rc = upload(fs, S.d_meta, S.h_stage);
+    if (!rc && !fs2.h.empty()) rc = upload(fs2, S.d_meta + meta_bytes, S.h_stage + meta_bytes);
+    // the chunk: lane 1 forks from lane 0's stream after the uploads and
+    // initial states, and lane 0 joins it before the copy-outs; exact grids,
+    // records only after sweeps where some job takes one
+    const bool two = !rc && !fs2.h.empty();
+    if (two && (cudaEventRecord(ev_fork, fs.stream) != cudaSuccess ||
+                cudaStreamWaitEvent(fs2.stream, ev_fork, 0) != cudaSuccess))
+      rc = fail(ISING_ECUDA, "lane fork failed");
+    if (!rc) {
       fs.L = S.L;
       rc = fs.enqueue_sweeps(0, chunk, false, false);
       if (!rc && launch_advance(S.L, grid_adv, chunk, fs.stream) != cudaSuccess)
         rc = fail(ISING_ECUDA, "advance launch failed");
+    }
+    if (!rc && two) {
+      fs2.L = S.L2;
+      rc = fs2.enqueue_sweeps(0, chunk, false, false);
+      if (!rc && launch_advance(S.L2, grid_adv, chunk, fs2.stream) != cudaSuccess)
+        rc = fail(ISING_ECUDA, "advance launch failed");
+      if (!rc && (cudaEventRecord(ev_join, fs2.stream) != cudaSuccess ||
+                  cudaStreamWaitEvent(fs.stream, ev_join, 0) != cudaSuccess))
+        rc = fail(ISING_ECUDA, "lane join failed");
     }
     for (size_t i = 0; !rc && i < fin.size(); i++) {
       Job* j = fin[i];
@@ -399,6 +449,21 @@ void ising_server::loop() {
   }
 }
 
+void ising_server::release_lanes() {
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  ev_fork = ev_join = nullptr;
+  for (FilmSet* f : {&fs, &fs2}) {  // the arena is freed once, below, not by the film sets
+    f->pool = nullptr;
+    f->rec = nullptr;
+    f->part = nullptr;
+  }
+  if (arena_dev) cudaFree(arena_dev);
+  arena_dev = nullptr;
+  fs2.release();
+  fs.release();
+}
+
 void ising_server::release_slots() {
   for (Slot& s : slot) {
     if (s.done) cudaEventDestroy(s.done);
@@ -422,17 +487,26 @@ int ising_server_create(size_t hbm_budget_bytes, uint32_t chunk_sweeps, ising_se
   s->budget = hbm_budget_bytes / kAlign * kAlign;
   s->chunk = chunk_sweeps;
   int rc = s->fs.init_device();
-  if (rc) { delete s; return rc; }
+  if (!rc) rc = s->fs2.init_device();
+  if (rc) {
+    s->fs2.release();
+    s->fs.release();
+    delete s;
+    return rc;
+  }
   if (cudaMalloc(&s->arena_dev, s->budget) != cudaSuccess) {
     cudaGetLastError();
+    s->fs2.release();
     s->fs.release();
     delete s;
     return fail(ISING_ENOMEM, "cannot allocate the %zu-byte device arena", hbm_budget_bytes);
   }
   s->arena.reset(s->budget);
-  s->fs.pool = reinterpret_cast<uint32_t*>(s->arena_dev);
-  s->fs.rec = reinterpret_cast<int64_t*>(s->arena_dev);
-  s->fs.part = reinterpret_cast<int64_t*>(s->arena_dev);
+  for (FilmSet* f : {&s->fs, &s->fs2}) {
+    f->pool = reinterpret_cast<uint32_t*>(s->arena_dev);
+    f->rec = reinterpret_cast<int64_t*>(s->arena_dev);
+    f->part = reinterpret_cast<int64_t*>(s->arena_dev);
+  }
   s->grid_upd = s->fs.upd_grid_max();
   s->grid_meas = s->fs.meas_grid_max();
   s->grid_fin = (uint32_t)(2 * s->fs.n_sm);
@@ -440,12 +514,13 @@ int ising_server_create(size_t hbm_budget_bytes, uint32_t chunk_sweeps, ising_se
   for (Slot& sl : s->slot)
     if (!rc && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
       rc = fail(ISING_ECUDA, "event creation failed");
+  if (!rc && (cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = fail(ISING_ECUDA, "event creation failed");
   if (!rc) rc = s->ensure_capacity(1, 1, 1);
   if (rc) {
     s->release_slots();
-    cudaFree(s->arena_dev);
-    s->fs.pool = nullptr; s->fs.rec = nullptr; s->fs.part = nullptr;
-    s->fs.release();
+    s->release_lanes();
     delete s;
     return rc;
   }
@@ -577,12 +652,9 @@ int ising_server_destroy(ising_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   if (s->fs.stream) cudaStreamSynchronize(s->fs.stream);
+  if (s->fs2.stream) cudaStreamSynchronize(s->fs2.stream);
   s->release_slots();
-  s->fs.pool = nullptr;
-  s->fs.rec = nullptr;
-  s->fs.part = nullptr;
-  if (s->arena_dev) cudaFree(s->arena_dev);
-  s->fs.release();
+  s->release_lanes();
   delete s;
   return ISING_OK;
 }
