@@ -72,8 +72,9 @@ enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
  * RESIDENT  one block keeps the whole film in shared memory for a whole
  *           ising_sweep call (films of at most 65536 spins whose packed
  *           planes fit in 48 KiB);
- * GRID_1    two grid launches per sweep (plus the record kernels), one
- *           32-site word per thread: the shortest launch latency;
+ * GRID_1    two grid launches per sweep, one 32-site word per thread: the
+ *           shortest launch latency.  A recorded sweep's second launch also
+ *           sums the record, and a small kernel writes it;
  * GRID_2    the same with two words per thread, which overlaps one word's
  *           loads with the other's arithmetic;
  * GRID_Q    the same with four threads per word, each drawing two of its
