@@ -24,10 +24,16 @@ from . import analysis as A
 from .binding import Batch, series_energy, series_mean, ti_surface_field
 
 
-def run(workload, use_graph=True):
-    """All films of the set in one batch; returns one record series per film."""
+def run(workload, use_graph=True, autotune=True):
+    """All films of the set in one batch (the library's default lanes), its
+    launch shape autotuned unless autotune is False and its record rings
+    sized for the whole run; returns one record series per film.  The
+    records do not depend on the shape or the lanes."""
     b = Batch(workload["jobs"])
     try:
+        if autotune:
+            b.autotune()
+        b.reserve_records(workload["n_sweeps"])
         b.sweep(workload["n_sweeps"], use_graph)
         return [b.read_series(i) for i in range(len(workload["jobs"]))]
     finally:
