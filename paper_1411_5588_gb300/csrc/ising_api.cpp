@@ -153,13 +153,19 @@ int FilmSet::upload() {
   const size_t nf = h.size();
   const size_t bytes = sizeof(LaunchHdr) + nf * sizeof(FilmDesc) + (hh.upd_blocks + hh.meas_blocks) * sizeof(uint32_t);
   if (bytes > meta_bytes) {
+    const size_t cap = std::max(bytes, meta_bytes * 2);
     if (d_meta) {
       ISG_CK(cudaStreamSynchronize(stream));
-      ISG_CK(cudaFree(d_meta));
+      const cudaError_t e = cudaFree(d_meta);
       d_meta = nullptr;
+      meta_bytes = 0;  // nothing held until the new area is allocated
+      if (e != cudaSuccess) return fail(ISING_ECUDA, "cudaFree: %s", cudaGetErrorString(e));
     }
-    const size_t cap = std::max(bytes, meta_bytes * 2);
-    ISG_CK(cudaMalloc(&d_meta, cap));
+    if (cudaMalloc(&d_meta, cap) != cudaSuccess) {
+      cudaGetLastError();
+      d_meta = nullptr;
+      return fail(ISING_ENOMEM, "cannot allocate %zu bytes of launch descriptors", cap);
+    }
     meta_bytes = cap;
   }
   staging.resize(bytes);
@@ -309,13 +315,18 @@ int ensure_ring(ising* h, uint64_t extra) {
   int64_t* nr = nullptr;
   if (cudaMalloc(&nr, cap * rl * sizeof(int64_t)) != cudaSuccess)
     return fail(ISING_ENOMEM, "cannot allocate %llu records", (unsigned long long)cap);
-  ISG_CK(cudaStreamSynchronize(h->fs.stream));
-  for (uint64_t i = 0; i < pending; i++) {
+  cudaError_t e = cudaStreamSynchronize(h->fs.stream);
+  for (uint64_t i = 0; e == cudaSuccess && i < pending; i++) {
     const uint64_t slot = (h->rec_read + i) % d.rec_cap;
-    ISG_CK(cudaMemcpyAsync(nr + i * rl, h->fs.rec + slot * rl, rl * sizeof(int64_t), cudaMemcpyDeviceToDevice,
-                           h->fs.stream));
+    e = cudaMemcpyAsync(nr + i * rl, h->fs.rec + slot * rl, rl * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                        h->fs.stream);
   }
-  ISG_CK(cudaStreamSynchronize(h->fs.stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->fs.stream);
+  if (e != cudaSuccess) {  // the old ring stays in place
+    cudaStreamSynchronize(h->fs.stream);
+    cudaFree(nr);
+    return fail(ISING_ECUDA, "record ring copy: %s", cudaGetErrorString(e));
+  }
   if (h->fs.rec) cudaFree(h->fs.rec);
   h->fs.rec = nr;
   h->fs.rec_words = cap * rl;

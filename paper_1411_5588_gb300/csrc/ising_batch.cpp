@@ -70,25 +70,38 @@ int lane_ensure_rings(Lane* b, const std::vector<uint64_t>& extra) {
     cudaGetLastError();
     return fail(ISING_ENOMEM, "cannot allocate %zu record words", total);
   }
-  ISG_CK(cudaStreamSynchronize(fs.stream));
-  size_t off = 0;
+  // copy the unread records first; the films move to the new rings only once
+  // every copy has finished, so a failure leaves the old rings in place
+  cudaError_t e = cudaStreamSynchronize(fs.stream);
+  std::vector<size_t> off(nf);
+  size_t o = 0;
   for (size_t f = 0; f < nf; f++) {
-    FilmDesc& d = fs.h[f];
+    const FilmDesc& d = fs.h[f];
     const size_t rl = record_len(d);
     const uint64_t pending = b->rec_written[f] - b->rec_read[f];
-    for (uint64_t i = 0; i < pending; i++) {
+    for (uint64_t i = 0; e == cudaSuccess && i < pending; i++) {
       const uint64_t slot = (b->rec_read[f] + i) % d.rec_cap;
-      ISG_CK(cudaMemcpyAsync(nr + off + i * rl, fs.rec + d.rec_off + slot * rl, rl * sizeof(int64_t),
-                             cudaMemcpyDeviceToDevice, fs.stream));
+      e = cudaMemcpyAsync(nr + o + i * rl, fs.rec + d.rec_off + slot * rl, rl * sizeof(int64_t),
+                          cudaMemcpyDeviceToDevice, fs.stream);
     }
-    d.rec_off = off;
+    off[f] = o;
+    o += cap[f] * rl;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(fs.stream);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(fs.stream);
+    cudaFree(nr);
+    return fail(ISING_ECUDA, "record ring copy: %s", cudaGetErrorString(e));
+  }
+  for (size_t f = 0; f < nf; f++) {
+    FilmDesc& d = fs.h[f];
+    const uint64_t pending = b->rec_written[f] - b->rec_read[f];
+    d.rec_off = off[f];
     d.rec_cap = (uint32_t)cap[f];
     d.rec_next = (uint32_t)pending;
     b->rec_read[f] = 0;
     b->rec_written[f] = pending;
-    off += cap[f] * rl;
   }
-  ISG_CK(cudaStreamSynchronize(fs.stream));
   if (fs.rec) cudaFree(fs.rec);
   fs.rec = nr;
   fs.rec_words = total;

@@ -168,7 +168,9 @@ struct ising_server {
 // Descriptor buffers large enough for nf films, nu update and nm measurement
 // blocks (grown only between chunks, once no chunk uses them).
 int ising_server::ensure_capacity(uint32_t nf, uint32_t nu, uint32_t nm) {
-  if (nf <= cap_films && nu <= cap_upd && nm <= cap_meas && slot[0].d_meta) return ISING_OK;
+  bool held = true;  // every slot's areas (a failed allocation leaves some out)
+  for (const Slot& s : slot) held = held && s.d_meta && s.h_stage;
+  if (nf <= cap_films && nu <= cap_upd && nm <= cap_meas && held) return ISING_OK;
   for (Slot& s : slot) {
     int rc = wait_slot(s);
     if (rc) return rc;
@@ -193,8 +195,16 @@ int ising_server::ensure_capacity(uint32_t nf, uint32_t nu, uint32_t nm) {
     if (s.h_stage) cudaFreeHost(s.h_stage);
     s.d_meta = nullptr;
     s.h_stage = nullptr;
-    ISG_CK(cudaMalloc(&s.d_meta, 2 * meta_bytes));
-    ISG_CK(cudaMallocHost(&s.h_stage, 2 * meta_bytes));
+    if (cudaMalloc(&s.d_meta, 2 * meta_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s.d_meta = nullptr;
+      return fail(ISING_ENOMEM, "cannot allocate %zu bytes of launch descriptors", 2 * meta_bytes);
+    }
+    if (cudaMallocHost(&s.h_stage, 2 * meta_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s.h_stage = nullptr;
+      return fail(ISING_ENOMEM, "cannot allocate %zu bytes of pinned staging", 2 * meta_bytes);
+    }
     carve(s.d_meta, s.L);
     carve(s.d_meta + meta_bytes, s.L2);
   }
