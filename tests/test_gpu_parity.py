@@ -368,6 +368,42 @@ def test_lanes_give_the_same_chains(lanes):
     b.close()
 
 
+def test_batch_rings_grow_with_wrapped_unread_records():
+    """Two lanes; records every 1, 2, 1 and 3 sweeps; partial reads leave
+    unread records that wrap round a ring, and a later call grows that ring
+    (graph and direct calls).  Every film's full series, read in pieces, and
+    its final spins equal the oracle's."""
+    geoms = [(6, 8, 40), (5, 6, 34), (8, 10, 64), (4, 9, 96)]
+    every = [1, 2, 1, 3]
+    specs = [dict(Lx=Lx, Ly=Ly, Lz=Lz, T=2.6 + 0.2 * i, H1=0.15 * i, seed=17, replica=i, measure_every=m,
+                  init_kind=ig.INIT_SLAB_Y, flip_p=0.02) for i, ((Lx, Ly, Lz), m) in enumerate(zip(geoms, every))]
+    b = ig.Batch(specs, lanes=2)
+    got = [[] for _ in specs]
+
+    def read(i, cap=None):
+        r = b.read_series(i) if cap is None else b.read_series(i, cap=cap)
+        got[i].append(r)
+        return len(r)
+
+    b.sweep(100, True)  # rings of the every-sweep films grow from 64 records
+    assert read(0, cap=30) == 30
+    read(1)
+    read(3, cap=5)
+    b.sweep(20, False)
+    b.sweep(30, False)  # film 0's unread records now wrap round its ring
+    assert read(0, cap=50) == 50
+    b.sweep(150, True)  # ...and that ring grows with them in it
+    for i in range(len(specs)):
+        read(i)
+    for i, sp in enumerate(specs):
+        o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], replica=sp["replica"])
+        o.init(sp["init_kind"], sp["flip_p"])
+        want = o.sweep(300, sp["measure_every"])
+        assert np.array_equal(np.concatenate(got[i]), want), i
+        assert np.array_equal(b.get_spins(i), o.get_spins()), i
+    b.close()
+
+
 def test_lanes_join_the_batch_stream():
     """Work queued on the batch's stream after a sweep sees every lane's
     films swept: a torch copy of a lane-1 film's spins taken on that stream
