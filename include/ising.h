@@ -139,7 +139,9 @@ int ising_set_sweep(ising *h, uint64_t sweep);
 
 /* Make room for n_records more pending records, so that later ising_sweep
  * calls do not grow the series (growth is a device allocation, a copy of the
- * pending records and a synchronisation).  ENOMEM. */
+ * pending records and a synchronisation).  ENOMEM when the series would pass
+ * 2^32 - 16 records or the device cannot hold it; a refused or failed growth
+ * leaves the series and the pending records as they were. */
 int ising_reserve_records(ising *h, uint64_t n_records);
 
 /* Pin the launch shape of this handle's ising_sweep calls (ISING_SHAPE_*;
@@ -244,7 +246,8 @@ int ising_batch_set_stream(ising_batch *b, void *cuda_stream);
 int ising_batch_sweep(ising_batch *b, uint64_t n_sweeps, int use_graph);
 
 /* Room for n_records more pending records of every film that records (see
- * ising_reserve_records).  ENOMEM. */
+ * ising_reserve_records).  ENOMEM, with every film's series as it was (lanes
+ * grown before the refusal keep their larger rings). */
 int ising_batch_reserve_records(ising_batch *b, uint64_t n_records);
 
 /* Launch shape of the batch's grid kernels: GRID_1, GRID_2, GRID_Q, or AUTO (the

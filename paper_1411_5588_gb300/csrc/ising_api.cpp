@@ -161,11 +161,8 @@ int FilmSet::upload() {
       meta_bytes = 0;  // nothing held until the new area is allocated
       if (e != cudaSuccess) return fail(ISING_ECUDA, "cudaFree: %s", cudaGetErrorString(e));
     }
-    if (cudaMalloc(&d_meta, cap) != cudaSuccess) {
-      cudaGetLastError();
-      d_meta = nullptr;
+    if (dev_alloc(&d_meta, cap) != cudaSuccess)
       return fail(ISING_ENOMEM, "cannot allocate %zu bytes of launch descriptors", cap);
-    }
     meta_bytes = cap;
   }
   staging.resize(bytes);
@@ -276,7 +273,8 @@ struct ising {
 namespace {
 
 int ensure_stage(ising* h) {
-  if (!h->d_stage) ISG_CK(cudaMalloc(&h->d_stage, (size_t)h->d().Lx * h->d().Ly * h->d().Lz));
+  if (!h->d_stage && dev_alloc(&h->d_stage, (size_t)h->d().Lx * h->d().Ly * h->d().Lz) != cudaSuccess)
+    return fail(ISING_ENOMEM, "cannot allocate the spin staging buffer");
   return ISING_OK;
 }
 
@@ -313,7 +311,7 @@ int ensure_ring(ising* h, uint64_t extra) {
   if (cap > 0xFFFFFFF0ull) return fail(ISING_ENOMEM, "record series too long; read it out first");
   const size_t rl = record_len(d);
   int64_t* nr = nullptr;
-  if (cudaMalloc(&nr, cap * rl * sizeof(int64_t)) != cudaSuccess)
+  if (dev_alloc(&nr, cap * rl * sizeof(int64_t)) != cudaSuccess)
     return fail(ISING_ENOMEM, "cannot allocate %llu records", (unsigned long long)cap);
   cudaError_t e = cudaStreamSynchronize(h->fs.stream);
   for (uint64_t i = 0; e == cudaSuccess && i < pending; i++) {
@@ -364,10 +362,10 @@ int ising_create(int Lx, int Ly, int Lz, double J, double H1, double T, uint64_t
   if (rc) { delete h; return rc; }
   h->fs.layout();
   const size_t words = film_words(d);
-  if (cudaMalloc(&h->fs.pool, words * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc(&h->fs.part, part_len(d) * sizeof(int64_t)) != cudaSuccess ||
+  if (dev_alloc(&h->fs.pool, words * sizeof(uint32_t)) != cudaSuccess ||
+      dev_alloc(&h->fs.part, part_len(d) * sizeof(int64_t)) != cudaSuccess ||
       cudaMemset(h->fs.part, 0, part_len(d) * sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&h->d_direct, record_len(d) * sizeof(int64_t)) != cudaSuccess) {
+      dev_alloc(&h->d_direct, record_len(d) * sizeof(int64_t)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(h->d_direct);
     delete h;

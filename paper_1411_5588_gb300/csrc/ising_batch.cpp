@@ -66,10 +66,8 @@ int lane_ensure_rings(Lane* b, const std::vector<uint64_t>& extra) {
     total += c * record_len(fs.h[f]);
   }
   int64_t* nr = nullptr;
-  if (cudaMalloc(&nr, std::max<size_t>(total, 1) * sizeof(int64_t)) != cudaSuccess) {
-    cudaGetLastError();
+  if (dev_alloc(&nr, std::max<size_t>(total, 1) * sizeof(int64_t)) != cudaSuccess)
     return fail(ISING_ENOMEM, "cannot allocate %zu record words", total);
-  }
   // copy the unread records first; the films move to the new rings only once
   // every copy has finished, so a failure leaves the old rings in place
   cudaError_t e = cudaStreamSynchronize(fs.stream);
@@ -174,8 +172,8 @@ int lane_create(const std::vector<ising_job>& jobs, Lane** out) {
   fs.layout();
   size_t part = 0;
   for (auto& d : fs.h) part += part_len(d);
-  if (cudaMalloc(&fs.pool, words * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc(&fs.part, part * sizeof(int64_t)) != cudaSuccess ||
+  if (dev_alloc(&fs.pool, words * sizeof(uint32_t)) != cudaSuccess ||
+      dev_alloc(&fs.part, part * sizeof(int64_t)) != cudaSuccess ||
       cudaMemset(fs.part, 0, part * sizeof(int64_t)) != cudaSuccess) {
     cudaGetLastError();
     return drop(fail(ISING_ENOMEM, "device allocation of %zu words failed", words));
@@ -505,7 +503,8 @@ int ising_batch_get_spins(ising_batch* b, size_t i, int8_t* s) {
   if (!b || !s) return fail(ISING_EINVAL, "NULL argument");
   if (i >= b->jobs.size()) return fail(ISING_ENOTFOUND, "film %zu out of range", i);
   Lane* l = b->lane_of(i);
-  if (!l->d_stage) ISG_CK(cudaMalloc(&l->d_stage, l->stage_bytes));
+  if (!l->d_stage && dev_alloc(&l->d_stage, l->stage_bytes) != cudaSuccess)
+    return fail(ISING_ENOMEM, "cannot allocate the spin staging buffer");
   const FilmDesc& d = l->fs.h[b->index_in_lane(i)];
   ISG_CK(launch_unpack(d, l->fs.pool, l->d_stage, l->fs.stream));
   ISG_CK(cudaMemcpyAsync(s, l->d_stage, (size_t)d.Lx * d.Ly * d.Lz, cudaMemcpyDeviceToHost, l->fs.stream));

@@ -20,6 +20,28 @@ const char* last_error();
 // Polls a stream until it is idle or timeout_s passes (ETIMEOUT).
 int wait_stream(cudaStream_t st, double timeout_s);
 
+// cudaMalloc / cudaMallocHost that leave no error pending when they fail: a
+// failed allocation stays CUDA's last error, and the next launch check would
+// report it again against an unrelated call.  *p is null after a failure.
+template <typename T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+  }
+  return e;
+}
+template <typename T>
+inline cudaError_t host_alloc(T** p, size_t bytes) {
+  const cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+  }
+  return e;
+}
+
 #define ISG_CK(call)                                                                        \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \

@@ -195,16 +195,10 @@ int ising_server::ensure_capacity(uint32_t nf, uint32_t nu, uint32_t nm) {
     if (s.h_stage) cudaFreeHost(s.h_stage);
     s.d_meta = nullptr;
     s.h_stage = nullptr;
-    if (cudaMalloc(&s.d_meta, 2 * meta_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      s.d_meta = nullptr;
+    if (dev_alloc(&s.d_meta, 2 * meta_bytes) != cudaSuccess)
       return fail(ISING_ENOMEM, "cannot allocate %zu bytes of launch descriptors", 2 * meta_bytes);
-    }
-    if (cudaMallocHost(&s.h_stage, 2 * meta_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      s.h_stage = nullptr;
+    if (host_alloc(&s.h_stage, 2 * meta_bytes) != cudaSuccess)
       return fail(ISING_ENOMEM, "cannot allocate %zu bytes of pinned staging", 2 * meta_bytes);
-    }
     carve(s.d_meta, s.L);
     carve(s.d_meta + meta_bytes, s.L2);
   }
@@ -380,7 +374,7 @@ void ising_server::loop() {
         if (S.h_res) cudaFreeHost(S.h_res);
         S.h_res = nullptr;
         S.res_cap = std::max(need, 2 * S.res_cap);
-        if (cudaMallocHost(&S.h_res, S.res_cap) != cudaSuccess) {
+        if (host_alloc(&S.h_res, S.res_cap) != cudaSuccess) {
           S.res_cap = 0;
           rc = fail(ISING_ENOMEM, "cannot allocate %zu bytes of pinned result staging", need);
         }
@@ -504,8 +498,7 @@ int ising_server_create(size_t hbm_budget_bytes, uint32_t chunk_sweeps, ising_se
     delete s;
     return rc;
   }
-  if (cudaMalloc(&s->arena_dev, s->budget) != cudaSuccess) {
-    cudaGetLastError();
+  if (dev_alloc(&s->arena_dev, s->budget) != cudaSuccess) {
     s->fs2.release();
     s->fs.release();
     delete s;

@@ -114,6 +114,42 @@ def test_record_ring_grows_and_drains_in_order():
     g.close()
 
 
+def test_failed_ring_growth_leaves_the_film_usable():
+    """A record reservation no device can hold (2^32 - 256 records of 45
+    int64, about 1.5 TB) is refused with ENOMEM before anything changes: the
+    pending records, the later ones (through a real ring growth) and the
+    spins are still the oracle's."""
+    case = (40, 6, 64, ig.Y_GAPBC, ig.X_FREE, 0.4, 0.0, 3.0, ig.INIT_SLAB_Y, 0.02)
+    g, o = _pair(case)
+    g.sweep(30, 1)
+    with pytest.raises(ig.IsingError) as e:
+        g.reserve_records(0xFFFFFF00)
+    assert e.value.status == ig.ENOMEM
+    g.sweep(100, 1)
+    assert np.array_equal(g.read_series(), o.sweep(130, 1))
+    assert np.array_equal(g.get_spins(), o.get_spins())
+    g.close()
+
+
+def test_failed_batch_ring_growth_leaves_the_batch_usable():
+    """The same for a two-lane batch: the refused reservation (several TB)
+    leaves every film's rings, records and spins as the oracle has them."""
+    specs = [dict(Lx=40, Ly=4 + i, Lz=64, T=2.8 + 0.2 * i, H1=0.2, seed=23, replica=i, measure_every=1 + i,
+                  init_kind=ig.INIT_SLAB_Y, flip_p=0.02) for i in range(3)]
+    b = ig.Batch(specs, lanes=2)
+    b.sweep(30, False)
+    with pytest.raises(ig.IsingError) as e:
+        b.reserve_records(0xFFFFFF00)
+    assert e.value.status == ig.ENOMEM
+    b.sweep(100, True)
+    for i, sp in enumerate(specs):
+        o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], replica=sp["replica"])
+        o.init(sp["init_kind"], sp["flip_p"])
+        assert np.array_equal(b.read_series(i), o.sweep(130, sp["measure_every"])), i
+        assert np.array_equal(b.get_spins(i), o.get_spins()), i
+    b.close()
+
+
 def test_parameter_change_between_sweeps():
     case = (6, 6, 64, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 3.0, ig.INIT_RANDOM, 0.0)
     g, o = _pair(case)
