@@ -516,16 +516,19 @@ def main():
 
     e2e = None
     extras = {}
-    if rank == 0 and not args.no_extras:
-        # end to end through the C ABI: initial lattice from pinned host memory,
-        # each step's record copied back to pinned host memory on a copy
-        # stream, overlapping the next step's sweeps
+    if not args.no_extras:
+        # end to end through the C ABI on every rank: initial lattice from
+        # pinned host memory, each step's record copied back to pinned host
+        # memory on a copy stream, overlapping the next step's sweeps; the
+        # time is the maximum over ranks
         host = torch.from_numpy(film.get_spins()).pin_memory()
         rl = 5 + job["Lx"]
         host_rec = torch.zeros((args.steps, rl), dtype=torch.int64).pin_memory()
         copy_stream = torch.cuda.Stream()
         film.reserve_records(args.steps)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         lib = ig.lib()
         ig.check(lib.ising_set_spins(film._h, ig.binding.P(host.data_ptr())), "ising_set_spins")
@@ -535,13 +538,14 @@ def main():
             got += film.read_series_async(host_rec[i].data_ptr(), 1, copy_stream)
         copy_stream.synchronize()
         film.synchronize()
-        dt = time.perf_counter() - t0
+        dt = max_over_ranks(time.perf_counter() - t0, device="cuda")
         assert got == args.steps and int(host_rec[-1, 0]) > 0
-        e2e = {"value": sites * SWEEPS_PER_STEP * args.steps / dt / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": sites / args.steps, "d2h_bytes_per_step": 8 * rl,
+        e2e = {"value": world * sites * SWEEPS_PER_STEP * args.steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": world * sites / args.steps, "d2h_bytes_per_step": world * 8 * rl,
                "note": "initial int8 lattice uploaded once from pinned memory (bytes spread over the steps); "
                        "each step's record copied to pinned host memory (ising_read_series_async on a copy "
-                       "stream, overlapping the next step)"}
+                       "stream, overlapping the next step); all ranks, time = max over ranks"}
+    if rank == 0 and not args.no_extras:
         for name, fn in (("batched", lambda: batched_vs_plain(ig, WL, torch)),
                          ("serving", lambda: serving(ig, WL, n_jobs=args.serve_jobs)),
                          ("serving_capacity", lambda: serving_capacity(ig, WL)),
