@@ -558,6 +558,8 @@ def main():
                 extras[name] = {"error": repr(exc)}
     film.close()
     if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     # per step: two half-sweep launches per sweep (the last one of the step
     # also takes the record sums), record_kernel, and the sweep-counter advance
