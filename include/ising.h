@@ -42,8 +42,11 @@
  *
  * Errors: every call returns an ISING_* status; nothing aborts, and no
  * kernel traps.  ising_last_error() gives a one-line message for the calling
- * thread.  Device waits inside the library are bounded and report
- * ISING_ETIMEOUT.  A handle may be used from one host thread at a time.
+ * thread.  A call that fails with ISING_ECUDA or ISING_ENOMEM has consumed
+ * the CUDA runtime's pending error, so the failure does not resurface in a
+ * later call (a sticky error, which leaves the context unusable, persists).
+ * Device waits inside the library are bounded and report ISING_ETIMEOUT.  A
+ * handle may be used from one host thread at a time.
  */
 #ifndef ISING_GB300_H
 #define ISING_GB300_H

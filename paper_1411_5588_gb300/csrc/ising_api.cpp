@@ -28,6 +28,9 @@ int fail(int code, const char* fmt, ...) {
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
   g_err = buf;
+  // a failed runtime call stays CUDA's last error; consume it here so that a
+  // later launch check does not report it again (sticky errors persist)
+  if (code == ISING_ECUDA || code == ISING_ENOMEM) cudaGetLastError();
   return code;
 }
 
