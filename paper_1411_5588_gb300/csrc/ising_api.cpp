@@ -68,9 +68,9 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   d.x_pbc = x_mode == ISING_X_PBC ? 1u : 0u;
   d.key0 = (uint32_t)seed ^ (uint32_t)(seed >> 32);
   d.key1 = replica;
-  for (int r = 0; r < 10; r++) {
-    d.rk0[r] = d.key0 + (uint32_t)r * kWeyl0;
-    d.rk1[r] = d.key1 + (uint32_t)r * kWeyl1;
+  for (uint32_t k = 0; k < 10; k++) {  // round keys: key + k * Weyl constant
+    d.rk0[k] = d.key0 + k * kWeyl0;
+    d.rk1[k] = d.key1 + k * kWeyl1;
   }
   d.upd_items = d.Lx * (d.Ly - 1) * d.W;
   d.meas_bpl = std::max<uint32_t>(1, (d.Ly * d.W + kMeasureItemsPerBlock - 1) / kMeasureItemsPerBlock);
