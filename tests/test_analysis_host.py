@@ -103,6 +103,10 @@ def test_stiffness_step_and_roughening(rng):
     th = math.pi / 2 - np.linspace(0.01, 0.1, 8)
     g = 1.5 + 0.6 * (math.pi / 2 - th) + 1e-3 * rng.normal(size=8)
     assert close(A.step_free_energy(th, g), OA.step_free_energy(th, g))
+    phis = np.linspace(0.01, 0.1, 4)
+    th = np.concatenate([math.pi / 2 - phis, math.pi / 2 + phis])  # both sides of pi/2
+    g = 1.5 + 0.6 * np.abs(math.pi / 2 - th) + 1e-3 * rng.normal(size=8)
+    assert close(A.step_free_energy(th, g), OA.step_free_energy(th, g))
     T = np.array([2.5, 2.6, 2.7, 3.0])
     k = T * (math.pi / 2) * (1 - 1.5 * np.sqrt((T - 2.45) / 4.51)) + 1e-3 * rng.normal(size=4)
     assert close(A.roughening_kappa_fit(T, k, 2.45, 4.51), OA.roughening_kappa_fit(T, k, 2.45, 4.51))

@@ -335,6 +335,17 @@ def test_step_free_energy_at_zero_temperature():
     assert abs(fs - 2.0) < 0.03 and abs(g0 - 2.0) < 1e-3
 
 
+def test_step_free_energy_on_both_sides_of_the_cusp():
+    """Eq. 26 takes the tilt's magnitude: a tilt either way from pi/2 costs
+    the same, so the T = 0 tension gamma0 (|sin| + |cos|) sampled on both
+    sides of the flat orientation still gives f_s = gamma0."""
+    phi = np.linspace(0.002, 0.02, 10)
+    th = np.concatenate([math.pi / 2 - phi, math.pi / 2 + phi])
+    g = 2.0 * (np.abs(np.sin(th)) + np.abs(np.cos(th)))
+    fs, g0 = OA.step_free_energy(th, g)
+    assert abs(fs - 2.0) < 0.03 and abs(g0 - 2.0) < 1e-3
+
+
 def test_step_model_limits():
     """Eqs. 28-32: no tilt at H1 = 0; at H1 = H1* the up-step weight equals
     the flat one (which defines Eq. 32); a strong field saturates at one
