@@ -9,6 +9,10 @@ oracle/ti.py. It shares no code with the product and imports nothing from it.
   interface_tension   Sec. II C (Eqs. 19-20)
   line_tension        Sec. IV (Eqs. 21-22)
   stiffness_and_steps Secs. III B, III C (Eqs. 23-24, 26, 28-32)
+
+The composition (which films feed which terms, which record columns, the
+per-site normalisations, the integration limits) is pinned on hand-built
+records whose reductions have closed forms (tests/test_oracle_workflows.py).
 """
 from __future__ import annotations
 

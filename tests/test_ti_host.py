@@ -9,10 +9,11 @@ import paper_1411_5588_gb300 as ig
 from oracle import ti as OT
 
 
+@pytest.mark.parametrize("a,b", [(0.0, 0.75), (0.3, 1.1), (-1.0, 2.0)])
 @pytest.mark.parametrize("n", [1, 2, 5, 16, 33])
-def test_gauss_legendre_exact_for_polynomials(n):
-    """n nodes integrate every polynomial of degree <= 2n-1 exactly."""
-    a, b = 0.0, 0.75
+def test_gauss_legendre_exact_for_polynomials(n, a, b):
+    """n nodes integrate every polynomial of degree <= 2n-1 exactly, on
+    intervals that start at 0 and elsewhere."""
     for x, w in (ig.gauss_legendre(n, a, b), OT.gauss_legendre(n, a, b)):
         assert abs(w.sum() - (b - a)) < 1e-14
         assert np.allclose(x, (a + b) - x[::-1], atol=1e-15)  # symmetric about the midpoint
