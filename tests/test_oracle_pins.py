@@ -251,6 +251,33 @@ def test_sweep_counter_convention():
                 assert s[kx - 1, ky - 1, z0] == (-1 if u < thr else 1)
 
 
+def test_acceptance_boundary_is_strict():
+    """The Metropolis reading with a 32-bit word takes a move iff u <
+    floor(exp(-dE/T) 2^32), so that it is accepted with probability exactly
+    thr / 2^32: the word equal to the threshold is rejected and the one below
+    it accepted (a chain could meet that word only once in 2^32 draws, so no
+    statistical pin sees the difference); dE <= 0 is always accepted."""
+    for dE, T in ((4.0, 3.0), (12.0, 2.2), (0.5, 0.7), (8.0, 1e-3 * 2 ** 10)):
+        thr = math.floor(math.ldexp(math.exp(-dE / T), 32))
+        assert 0 < thr < 2 ** 32
+        assert O.accept(dE, T, thr - 1) and not O.accept(dE, T, thr)
+    assert O.accept(0.0, 1.0, 0xFFFFFFFF) and O.accept(-4.0, 1.0, 0xFFFFFFFF)
+    assert not O.accept(4.0, 1e-3, 0)  # exp(-4000) floors to a zero threshold
+
+
+def test_records_fall_on_multiples_of_the_interval():
+    """A record is taken after every completed sweep whose count is a
+    multiple of the interval, the count running from 0 across calls (and from
+    wherever it was set)."""
+    f = O.Film(4, 6, 8, 1.0, 0.3, 3.0, 5)
+    f.init(O.INIT_RANDOM)
+    assert list(f.sweep(10, 3)[:, 0]) == [3, 6, 9]
+    assert list(f.sweep(5, 3)[:, 0]) == [12, 15]
+    f.sweep_count = 100
+    assert list(f.sweep(7, 4)[:, 0]) == [104]
+    assert list(f.sweep(2, 1)[:, 0]) == [108, 109]
+
+
 # ------------------------------------------------------- transition matrix
 
 def test_four_phase_schedule_preserves_boltzmann():
