@@ -55,3 +55,60 @@ def test_checked_build_has_no_out_of_range_access():
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["checked"] and out["films"] > 0
     assert out["count"] == 0, f"out-of-range lattice accesses: {out}"
+
+
+MAX_CHILD = r"""
+import json, sys
+sys.path.insert(0, __ROOT__)
+import torch
+import paper_1411_5588_gb300.binding as bd
+bd.LIB_PATH = __LIB__
+import paper_1411_5588_gb300 as ig
+# 16384 x 32767 rows of 4 full words: 2^31 - 65536 words per parity plane,
+# just under the largest film the library accepts (137e9 spins, 17 GB)
+Lx, Ly, Lz = 16384, 32767, 256
+film = ig.Film(Lx, Ly, Lz, 1.0, 0.4, float("inf"), 3)
+film.init(ig.INIT_RANDOM)
+n = film.packed_words()
+before = torch.empty(n, dtype=torch.int32, device="cuda")
+after = torch.empty_like(before)
+film.get_packed_device(before.data_ptr())
+r0 = film.measure()
+film.sweep(1, 1)
+film.get_packed_device(after.data_ptr())
+r1 = film.read_series()[0]
+film.synchronize()
+flipped = True
+step = 1 << 28
+for i in range(0, n, step):
+    flipped = flipped and bool(torch.equal(after[i:i + step], torch.bitwise_not(before[i:i + step])))
+checked, count, first = ig.check_counters()
+film.close()
+print(json.dumps({"checked": checked, "count": count, "first": first, "words": n, "flipped": flipped,
+                  "r0": [int(v) for v in r0[:8]], "r1": [int(v) for v in r1[:8]],
+                  "m_negated": bool((r1[5:] == -r0[5:]).all())}))
+"""
+
+
+def test_largest_film_flips_every_site_at_infinite_temperature():
+    """The largest class of film (just under 2^31 words per parity plane, where
+    32-bit word indices are tightest), in the checked build: at beta = 0 every
+    move is taken, so one sweep flips every site exactly once (each site sits
+    in exactly one of the four phases).  The packed lattice must come out as
+    its bitwise complement, the bond sum unchanged and every magnetisation sum
+    negated, with not one out-of-range access."""
+    from paper_1411_5588_gb300 import build
+    lib = build.build(checked=True)
+    code = MAX_CHILD.replace("__ROOT__", repr(ROOT)).replace("__LIB__", repr(lib))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1800)
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["checked"] and out["count"] == 0, f"out-of-range lattice accesses: {out}"
+    assert out["words"] == 2 * 16384 * 32767 * 4
+    assert out["flipped"]
+    r0, r1 = out["r0"], out["r1"]
+    assert r0[0] == 0 and r1[0] == 1
+    assert r1[1] == r0[1]  # B
+    assert r1[2:5] == [-v for v in r0[2:5]]  # M, M1, Mn
+    assert out["m_negated"]
+    assert abs(r0[2]) < 16384 * 32767 * 256 // 100  # a random start
