@@ -82,3 +82,37 @@ def test_batch_lanes_above_the_limit_are_einval():
     with pytest.raises(ig.IsingError) as e:
         ig.Batch([spec], lanes=ig.MAX_LANES + 1)
     assert e.value.status == ig.EINVAL
+
+
+@pytest.mark.skipif(_has_gpu(), reason="checks behaviour without a device")
+def test_film_size_limit_is_exact():
+    """At most 2^31 words per parity plane: 16384 x 32768 rows of four words
+    reach it and are refused before any device call (EINVAL); one row fewer
+    passes the check and only then meets the missing device (ECUDA)."""
+    import paper_1411_5588_gb300 as ig
+    with pytest.raises(ig.IsingError) as e:
+        ig.Film(16384, 32768, 256, 1.0, 0.0, 3.0, 1)
+    assert e.value.status == ig.EINVAL
+    with pytest.raises(ig.IsingError) as e:
+        ig.Film(16384, 32767, 256, 1.0, 0.0, 3.0, 1)
+    assert e.value.status == ig.ECUDA
+
+
+def test_batch_jobs_are_checked_before_any_device_call():
+    """Every job of a batch is validated before the first device call, so a
+    bad one is EINVAL even without a GPU (and with one, nothing is
+    allocated)."""
+    import paper_1411_5588_gb300 as ig
+    good = dict(Lx=4, Ly=4, Lz=8, T=3.0, H1=0.1, seed=1, replica=0)
+    bad = [dict(good, Lz=7), dict(good, Ly=1), dict(good, T=0.0), dict(good, y_mode=3),
+           dict(good, x_mode=ig.X_PBC, Lx=3), dict(good, init_kind=5),
+           dict(good, init_kind=ig.INIT_SLAB_Y, flip_p=1.5),
+           dict(good, init_kind=ig.INIT_SLAB_Y, flip_p=float("nan")),
+           dict(good, Lx=16384, Ly=32768, Lz=256)]
+    for spec in bad:
+        with pytest.raises(ig.IsingError) as e:
+            ig.Batch([good, spec])
+        assert e.value.status == ig.EINVAL, spec
+    with pytest.raises(ig.IsingError) as e:
+        ig.Batch([])
+    assert e.value.status == ig.EINVAL
