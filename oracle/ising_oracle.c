@@ -299,11 +299,14 @@ int64_t orc_sweep(orc_film *f, uint64_t n, uint32_t measure_every, int64_t *recs
     return nrec;
 }
 
-/* One record: {sweeps completed, B, M, M1, Mn, m(1), ..., m(Lx)}. */
+/* One record: {sweeps completed, B, M, M1, Mn, m(1), ..., m(Lx)}.  The
+ * layers are summed in parallel; every sum is an exact int64, so the record
+ * does not depend on the order or the thread count. */
 void orc_measure(const orc_film *f, int64_t *rec)
 {
     const int Lx = f->Lx, Ly = f->Ly, Lz = f->Lz;
     int64_t twice_b = 0, M = 0;
+#pragma omp parallel for schedule(static) reduction(+ : twice_b) if ((int64_t)Lx * Ly * Lz >= 65536)
     for (int kx = 1; kx <= Lx; kx++) {
         int64_t mk = 0;
         for (int ky = 1; ky <= Ly; ky++)
@@ -313,8 +316,8 @@ void orc_measure(const orc_film *f, int64_t *rec)
                 mk += s;
             }
         rec[5 + kx - 1] = mk;
-        M += mk;
     }
+    for (int kx = 1; kx <= Lx; kx++) M += rec[5 + kx - 1];
     rec[0] = (int64_t)f->sweep;
     rec[1] = twice_b / 2;
     rec[2] = M;
