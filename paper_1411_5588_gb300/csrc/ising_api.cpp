@@ -80,7 +80,7 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   d.active = 1;
   d.sweep_end = 0xFFFFFFFFu;
   fastdiv_magic(d.W, &d.divw_m, &d.divw_l);
-  fastdiv_magic(d.Ly - 1, &d.divy_m, &d.divy_l);
+  fastdiv_magic(d.Ly > 2 ? d.Ly - 2 : 1, &d.divy_m, &d.divy_l);  // rows ky = 2 .. Ly-1 of a layer
 }
 
 void build_tables(FilmDesc& d, double J, double H, double H1, double T) {
@@ -524,12 +524,13 @@ int ising_set_sweep(ising* h, uint64_t sweep) {
 int ising_check_counters(int* checked, uint64_t* count, uint64_t* first) {
   clear_error();
   if (!checked || !count || !first) return fail(ISING_EINVAL, "NULL argument");
-  unsigned long long c = 0, f = 0;
+  unsigned long long c = 0, f = 0, c2 = 0, f2 = 0;
   const int r = read_oob_counters(&c, &f);
-  if (r < 0) return fail(ISING_ECUDA, "cannot read the check counters");
+  const int r2 = read_noalloc_oob_counters(&c2, &f2);
+  if (r < 0 || r2 < 0) return fail(ISING_ECUDA, "cannot read the check counters");
   *checked = r;
-  *count = c;
-  *first = f;
+  *count = c + c2;
+  *first = f ? f : f2;
   return ISING_OK;
 }
 

@@ -52,7 +52,7 @@ struct FilmDesc {
   uint64_t rec_off;            // int64 offset of the record ring
   uint64_t part_off;           // int64 offset of this film's partial sums
   uint32_t divw_m, divw_l;     // n / W = (umulhi(n, m) + n) >> l  (n < 2^31)
-  uint32_t divy_m, divy_l;     // the same for Ly - 1
+  uint32_t divy_m, divy_l;     // the same for Ly - 2 (for 1 when Ly = 2)
   uint32_t thr[4][16];         // Metropolis thresholds [class][s + 2*n_aligned]
   uint32_t always[4];          // bit (s + 2*n_aligned): accept without a draw
   uint32_t has_never;          // some reachable entry has dE > 0 and thr = 0
@@ -181,6 +181,56 @@ __device__ __forceinline__ uint32_t shift_prev(uint32_t v, uint32_t prev) {
 // Word whose local site l holds site l+1 (z+1 neighbour of parity-1 sites).
 __device__ __forceinline__ uint32_t shift_next(uint32_t v, uint32_t next) {
   return (v >> 8) | ((v << 23) & 0x7F000000u) | (next << 31);
+}
+
+// Sum of S_i S_j over the valid sites of two words (nv = popc(valid)).
+__device__ __forceinline__ int word_bonds(uint32_t a, uint32_t b, uint32_t valid, int nv) {
+  return nv - 2 * __popc((a ^ b) & valid);
+}
+
+// Record contributions (Eqs. 1, 17) of word w of row (kxm1, kym1) (0-based)
+// of the planes A (z0 even) and B (z0 odd) with row stride Wp: the
+// magnetisation of its sites and their +x, +y (Eq. 11 wrap: partner row, sign
+// -1 unless PBC) and +z bonds, so that summing over all words counts every
+// bond once.  ld(plane, index, limit, site id) loads one word; the kernels'
+// checked builds test the index there.
+template <class Load>
+__device__ __forceinline__ void measure_word(Load ld, const uint32_t* A, const uint32_t* B, uint32_t Wp, uint32_t Lx,
+                                             uint32_t Ly, uint32_t W, uint32_t n, uint32_t last_mask, uint32_t x_pbc,
+                                             uint32_t y_mode, uint32_t kxm1, uint32_t kym1, uint32_t w, int& m,
+                                             int& bb) {
+  const uint32_t row = kxm1 * Ly + kym1;
+  const size_t base = (size_t)row * Wp + w;
+  const size_t lim = (size_t)Lx * Ly * Wp;
+  const bool last = (w + 1 == W);
+  const uint32_t valid = last ? last_mask : 0xFFFFFFFFu;
+  const int nv = __popc(valid);
+  const uint32_t a = ld(A, base, lim, 21), b = ld(B, base, lim, 22);
+  m = 2 * (__popc(a & valid) + __popc(b & valid)) - 2 * nv;
+  bb = 0;
+  // +x bond
+  if (kxm1 + 1 < Lx) {
+    const size_t nb = base + (size_t)Ly * Wp;
+    bb += word_bonds(a, ld(A, nb, lim, 23), valid, nv) + word_bonds(b, ld(B, nb, lim, 24), valid, nv);
+  } else if (x_pbc) {
+    const size_t nb = base - (size_t)(Lx - 1) * Ly * Wp;
+    bb += word_bonds(a, ld(A, nb, lim, 25), valid, nv) + word_bonds(b, ld(B, nb, lim, 26), valid, nv);
+  }
+  // +y bond
+  if (kym1 + 1 < Ly) {
+    bb += word_bonds(a, ld(A, base + Wp, lim, 27), valid, nv) + word_bonds(b, ld(B, base + Wp, lim, 28), valid, nv);
+  } else {
+    const uint32_t gkx = (y_mode == kYGapbc) ? (Lx - 1 - kxm1) : kxm1;
+    const size_t g = ((size_t)gkx * Ly) * Wp + w;
+    const int y = word_bonds(a, ld(A, g, lim, 29), valid, nv) + word_bonds(b, ld(B, g, lim, 30), valid, nv);
+    bb += (y_mode != kYPbc) ? -y : y;
+  }
+  // +z bonds: (2j, 2j+1) inside the word pair, (2j+1, 2j+2) through a shift
+  bb += word_bonds(a, b, valid, nv);
+  const size_t rbase = (size_t)row * Wp;
+  uint32_t an = shift_next(a, last ? ld(A, rbase, lim, 31) : ld(A, base + 1, lim, 32));
+  if (last && last_mask != 0xFFFFFFFFu) an |= (ld(A, rbase, lim, 33) & 1u) << bitpos((n - 1) & 31u);
+  bb += word_bonds(b, an, valid, nv);
 }
 
 #endif  // __CUDACC__

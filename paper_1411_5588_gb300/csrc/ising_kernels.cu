@@ -104,6 +104,16 @@ __device__ __forceinline__ void site_pair(uint32_t& lt, const char* tb, uint32_t
   }
 }
 
+// Decision of the site at bit Q + 8I (Philox call Q, word u).
+template <bool FAST, uint32_t Q, uint32_t I>
+__device__ __forceinline__ void site_one(uint32_t& lt, const char* tb, uint32_t Y, uint32_t u) {
+  uint32_t t;
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(tb);
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(base + __byte_perm(Y, 0, 0x4440 + I)));
+  if (FAST) or_if_le_c<1u << (Q + 8 * I)>(lt, u, t);
+  else or_if_lt_c<1u << (Q + 8 * I)>(lt, u, t);
+}
+
 // Per-launch constants of one film, kept in registers.
 struct FilmCtx {
   uint32_t* plane0;
@@ -111,6 +121,8 @@ struct FilmCtx {
   uint32_t Lx, Ly, n, W, Wp, y_mode, x_pbc, last_mask, last_calls;
   uint32_t plane_words;  // words of one plane (Lx * Ly * Wp), for checked builds
   uint32_t seam_same;    // the y-wrap bonds join sites of one colour (Lx+Ly even under Eq. 11, Ly odd otherwise)
+  // decision path of the film's words (kFull, kPartial, kSingle or kMixed)
+  __device__ __forceinline__ uint32_t path() const;
   const uint32_t* rk0;  // Philox round keys (constant bank or shared memory)
   const uint32_t* rk1;
   uint32_t colour, sweep;
@@ -344,17 +356,32 @@ __device__ __forceinline__ void add_layer_sums_shared(int* s_m, int* s_tot, cons
 // j - 1 of array 1, site j of array 1 meets site j + 1 of array 0, and the
 // row's ends meet through the periodic z wrap.
 template <bool FULL>
-__device__ __forceinline__ uint32_t z_shifted(const FilmCtx& c, const Fetched& f, uint32_t X) {
+__device__ __forceinline__ uint32_t z_shifted(const FilmCtx& c, const Fetched& f, uint32_t X, bool partial) {
   if (X == 0) {
     const uint32_t pw = (f.w > 0) ? f.za : (((f.za >> bitpos((c.n - 1) & 31u)) & 1u) << 31);
     return shift_prev(f.z0, pw);
   }
   uint32_t Zs = shift_next(f.z0, f.za);
-  if (!FULL) Zs |= (f.zf & 1u) << bitpos((c.n - 1) & 31u);
+  if (!FULL && partial) Zs |= (f.zf & 1u) << bitpos((c.n - 1) & 31u);
   return Zs;
 }
 
-template <bool FULL, bool FAST, bool QUARTER, bool MEAS = false>
+// Decision paths of a word, chosen per film (so that a warp issues one):
+//   kFull     32 valid sites, eight Philox calls;
+//   kPartial  the row's only word (W = 1), partial: the film's last_mask and
+//             last_calls (5..7 calls: calls Q and Q + 4 drawn together);
+//   kSingle   the same with at most four calls, each drawn alone;
+//   kMixed    rows of full words and a partial last word (W >= 2): each
+//             word's own mask and call count.
+enum : uint32_t { kFull = 0, kPartial = 1, kSingle = 2, kMixed = 3 };
+
+__device__ __forceinline__ uint32_t FilmCtx::path() const {
+  if (last_mask == 0xFFFFFFFFu) return kFull;
+  if (W >= 2) return kMixed;
+  return last_calls <= 4 ? kSingle : kPartial;
+}
+
+template <uint32_t PATH, bool FAST, bool QUARTER, bool MEAS = false>
 __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched& f,
                                                 const uint32_t* __restrict__ s_thr,
                                                 const uint32_t* __restrict__ s_alw, uint32_t qsel,
@@ -373,7 +400,9 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const uint32_t a1 = ~(S ^ f.xp) & xp_on;
   const uint32_t a2 = ~(S ^ f.ym ^ (ky > 1 ? 0u : negm));
   const uint32_t a3 = ~(S ^ f.yp ^ (ky < Ly ? 0u : negm));
-  const uint32_t Zs = z_shifted<FULL>(c, f, X);
+  constexpr bool FULL = PATH == kFull, SINGLE = PATH == kSingle;
+  const bool partial = PATH == kMixed ? (w + 1 == c.W) : !FULL;  // the word holds fewer than 32 sites
+  const uint32_t Zs = z_shifted<FULL>(c, f, X, partial);
   const uint32_t a4 = ~(S ^ f.z0);
   const uint32_t a5 = ~(S ^ Zs);
 
@@ -419,24 +448,35 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   U[2] = ((T0 >> 2) & 0x33333333u) | (T2 & 0xCCCCCCCCu);
   U[3] = ((T1 >> 2) & 0x33333333u) | (T3 & 0xCCCCCCCCu);
 
-  const uint32_t ncalls = FULL ? 8u : c.last_calls;
+  const uint32_t ncalls = FULL ? 8u : PATH == kMixed ? (partial ? c.last_calls : 8u) : c.last_calls;
   const uint32_t clsb = (cls * 64u) * 0x01010101u;  // byte offset of this class's table
   const char* tb = reinterpret_cast<const char*>(s_thr);
   const PhiloxRow pr(row, c.sweep, X, c.rk0, c.rk1);
   uint32_t lt = 0;
-  // calls Q and Q + 4 are drawn together (two independent Philox chains)
+  // calls Q and Q + 4 are drawn together (two independent Philox chains),
+  // except on the kSingle path
   auto calls = [&](auto qc, uint32_t Uq) {
     constexpr uint32_t Q = decltype(qc)::value;
     if (FULL || Q < ncalls) {
       uint32_t u[4], v[4];
-      pr.draw2(8u * w + Q, 8u * w + Q + 4, u, v);
-      const bool two = FULL || Q + 4 < ncalls;
-      const uint32_t Y = ((Uq << 2) & 0x3C3C3C3Cu) | clsb;
-      const uint32_t Y2 = ((Uq >> 2) & 0x3C3C3C3Cu) | clsb;
-      site_pair<FAST, Q, 0>(lt, tb, Y, Y2, u[0], v[0], two);
-      site_pair<FAST, Q, 1>(lt, tb, Y, Y2, u[1], v[1], two);
-      site_pair<FAST, Q, 2>(lt, tb, Y, Y2, u[2], v[2], two);
-      site_pair<FAST, Q, 3>(lt, tb, Y, Y2, u[3], v[3], two);
+      if (SINGLE) {
+        // a partial word of at most four calls: call Q alone
+        pr.draw(8u * w + Q, u);
+        const uint32_t Y = ((Uq << 2) & 0x3C3C3C3Cu) | clsb;
+        site_one<FAST, Q, 0>(lt, tb, Y, u[0]);
+        site_one<FAST, Q, 1>(lt, tb, Y, u[1]);
+        site_one<FAST, Q, 2>(lt, tb, Y, u[2]);
+        site_one<FAST, Q, 3>(lt, tb, Y, u[3]);
+      } else {
+        pr.draw2(8u * w + Q, 8u * w + Q + 4, u, v);
+        const bool two = FULL || Q + 4 < ncalls;
+        const uint32_t Y = ((Uq << 2) & 0x3C3C3C3Cu) | clsb;
+        const uint32_t Y2 = ((Uq >> 2) & 0x3C3C3C3Cu) | clsb;
+        site_pair<FAST, Q, 0>(lt, tb, Y, Y2, u[0], v[0], two);
+        site_pair<FAST, Q, 1>(lt, tb, Y, Y2, u[1], v[1], two);
+        site_pair<FAST, Q, 2>(lt, tb, Y, Y2, u[2], v[2], two);
+        site_pair<FAST, Q, 3>(lt, tb, Y, Y2, u[3], v[3], two);
+      }
     }
   };
   using Q0 = std::integral_constant<uint32_t, 0>;
@@ -474,8 +514,27 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
     calls(Q2{}, U[2]);
     calls(Q3{}, U[3]);
   }
-  const uint32_t valid = FULL ? 0xFFFFFFFFu : c.last_mask;
+  const uint32_t valid = FULL ? 0xFFFFFFFFu : PATH == kMixed ? (partial ? c.last_mask : 0xFFFFFFFFu) : c.last_mask;
   return (lt | alw) & valid;
+}
+
+// decide_word on the film's path (uniform across the film, so across a
+// warp).  PATHS4 = false keeps two bodies only (for the kernel whose register
+// budget has no room for more): full words on kFull, a partial last word on
+// kPartial, chosen per word.
+template <bool FAST, bool QUARTER, bool MEAS, bool PATHS4>
+__device__ __forceinline__ uint32_t decide_any(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
+                                               const uint32_t* s_alw, uint32_t qsel, uint32_t* stash) {
+  if (!PATHS4) {
+    if (f.w + 1 < c.W || c.last_mask == 0xFFFFFFFFu)
+      return decide_word<kFull, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+    return decide_word<kPartial, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+  }
+  const uint32_t path = c.path();
+  if (path == kFull) return decide_word<kFull, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+  if (path == kMixed) return decide_word<kMixed, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+  if (!QUARTER && path == kSingle) return decide_word<kSingle, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+  return decide_word<kPartial, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
 }
 
 __device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, uint32_t v) {
@@ -485,24 +544,30 @@ __device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, u
   ISG_ST(P, row * c.Wp + f.w, c.plane_words, 16, v);
 }
 
+// Word of update item `item`.  The first Lx * W items are the words of the
+// ky = 1 rows, whose threads then also update the wrap partner's word: kept
+// together, they fill whole warps instead of putting one lane that does twice
+// the work into a third of the warps of a small film.  The other items are
+// the rows ky = 2 .. Ly-1, layer by layer.  (dym, dyl) divide by Ly - 2 (by 1
+// when Ly = 2, which has no such rows).
 __device__ __forceinline__ void item_word(const FilmCtx& c, uint32_t item, uint32_t dwm, uint32_t dwl,
                                           uint32_t dym, uint32_t dyl, uint32_t& kx, uint32_t& ky, uint32_t& w) {
-  const uint32_t rp = fastdiv(item, dwm, dwl);
+  const uint32_t rp = fastdiv(item, dwm, dwl);  // the region boundary Lx * W is a whole number of rows
   w = item - rp * c.W;
-  const uint32_t kxm1 = fastdiv(rp, dym, dyl);
-  ky = rp - kxm1 * (c.Ly - 1) + 1;
-  kx = kxm1 + 1;
+  const bool pair = rp < c.Lx;
+  const uint32_t rq = pair ? 0u : rp - c.Lx;
+  const uint32_t q = fastdiv(rq, dym, dyl);
+  kx = (pair ? rp : q) + 1;
+  ky = pair ? 1u : rq - q * (c.Ly - 2) + 2;
 }
 
 // MEAS: also return the record sums of the word (r1) and of its partner word
 // (r2, ky = 1 only), using the thread's stash slots.
-template <bool FAST, bool MEAS = false>
+template <bool FAST, bool MEAS = false, bool PATHS4 = true>
 __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
                                                const uint32_t* s_alw, uint32_t* stash = nullptr,
                                                LayerSums* r1 = nullptr, LayerSums* r2 = nullptr) {
-  const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
-  const uint32_t fl = full ? decide_word<true, FAST, false, MEAS>(c, f, s_thr, s_alw, 0, stash)
-                           : decide_word<false, FAST, false, MEAS>(c, f, s_thr, s_alw, 0, stash);
+  const uint32_t fl = decide_any<FAST, false, MEAS, PATHS4>(c, f, s_thr, s_alw, 0, stash);
   const uint32_t v = f.S ^ fl;
   store_word(c, f, v);
   if (MEAS) *r1 = word_sums(c, f.kx, f.w, fl, v, stash);
@@ -513,8 +578,7 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
     Fetched g;
     fetch_word(c, kx2, c.Ly, f.w, g);
     if (MEAS) stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3], g) : 0u;
-    const uint32_t fl2 = full ? decide_word<true, FAST, false, MEAS>(c, g, s_thr, s_alw, 0, stash)
-                              : decide_word<false, FAST, false, MEAS>(c, g, s_thr, s_alw, 0, stash);
+    const uint32_t fl2 = decide_any<FAST, false, MEAS, PATHS4>(c, g, s_thr, s_alw, 0, stash);
     const uint32_t v2 = g.S ^ fl2;
     store_word(c, g, v2);
     if (MEAS) {
@@ -533,10 +597,8 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
                                                        uint32_t gmask, const uint32_t* s_thr,
                                                        const uint32_t* s_alw, uint32_t* stash, LayerSums& r1,
                                                        LayerSums& r2) {
-  const bool full = (f.w + 1 < c.W) || (c.last_mask == 0xFFFFFFFFu);
   uint32_t fl = 0;
-  if (on) fl = full ? decide_word<true, FAST, true, MEAS>(c, f, s_thr, s_alw, qsel, stash)
-                    : decide_word<false, FAST, true, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+  if (on) fl = decide_any<FAST, true, MEAS, true>(c, f, s_thr, s_alw, qsel, stash);
   if (!on) return;
   fl |= __shfl_xor_sync(gmask, fl, 1);
   fl |= __shfl_xor_sync(gmask, fl, 2);
@@ -551,8 +613,7 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
   Fetched g;
   fetch_word(c, kx2, c.Ly, f.w, g);
   if (MEAS) stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3], g) : 0u;
-  uint32_t fl2 = full ? decide_word<true, FAST, true, MEAS>(c, g, s_thr, s_alw, qsel, stash)
-                      : decide_word<false, FAST, true, MEAS>(c, g, s_thr, s_alw, qsel, stash);
+  uint32_t fl2 = decide_any<FAST, true, MEAS, true>(c, g, s_thr, s_alw, qsel, stash);
   fl2 |= __shfl_xor_sync(pmask, fl2, 1);
   fl2 |= __shfl_xor_sync(pmask, fl2, 2);
   const uint32_t v2 = g.S ^ fl2;
@@ -572,7 +633,7 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
 // sums go into the film's per-layer accumulators acc_of() (a pointer made
 // where it is used, not kept across the draws); s_stash holds kStashSlots
 // words per thread.
-template <bool FAST, uint32_t ITEMS, bool MEAS, typename AccOf>
+template <bool FAST, uint32_t ITEMS, bool MEAS, bool PATHS4, typename AccOf>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw,
@@ -615,7 +676,7 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 #pragma unroll
     for (uint32_t it = 0; it < NI; it++) {
       LayerSums r1, r2;
-      if (mine[it]) update_fetched<FAST, true>(c, fw[it], s_thr, s_alw, stash, &r1, &r2);
+      if (mine[it]) update_fetched<FAST, true, PATHS4>(c, fw[it], s_thr, s_alw, stash, &r1, &r2);
       add_layer_sums(acc_of(), r1);
       add_lane_sums(acc_of(), r2);
     }
@@ -623,7 +684,7 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
   }
 #pragma unroll
   for (uint32_t it = 0; it < NI; it++)
-    if (mine[it]) update_fetched<FAST>(c, fw[it], s_thr, s_alw);
+    if (mine[it]) update_fetched<FAST, false, PATHS4>(c, fw[it], s_thr, s_alw);
 }
 
 // Half-sweep of every film of a launch: block b handles words_per_block(ITEMS)
@@ -699,7 +760,9 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     const FilmDesc* sd = &s_d;
     auto acc_of = [part, sd]() { return reinterpret_cast<unsigned long long*>(part + acc_offset(*sd)); };
     const uint32_t first = (vb - s_d.upd_block_begin) * words_per_block(ITEMS);
-    sweep_block<FAST, ITEMS, MEAS>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
+    // two words per thread, and the exact table: the register budget keeps
+    // the two-path decision
+    sweep_block<FAST, ITEMS, MEAS, FAST && ITEMS != 2>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
                                    s_alw, meas, acc_of, s_stash);
   }
 }
@@ -734,7 +797,7 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
   c.seam_same = seam_joins_one_colour(d.Lx, d.Ly, d.y_mode);
   auto acc_of = [acc]() { return reinterpret_cast<unsigned long long*>(acc); };
-  sweep_block<FAST, ITEMS, MEAS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
+  sweep_block<FAST, ITEMS, MEAS, true>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
                                  d.divy_l, s_thr, s_alw, MEAS, acc_of, s_stash);
 }
 
@@ -742,51 +805,12 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
 
 namespace {
 
-__device__ __forceinline__ int bonds(uint32_t a, uint32_t b, uint32_t valid, int nv) {
-  return nv - 2 * __popc((a ^ b) & valid);
-}
-
-// Record contributions of word w of row (kxm1, kym1) (0-based) of the planes
-// A (z0 even) and B (z0 odd) with row stride Wp: the magnetisation of its
-// sites and their +x, +y (Eq. 11 wrap: partner row, sign -1 unless PBC) and
-// +z bonds.
-__device__ __forceinline__ void measure_word(const uint32_t* A, const uint32_t* B, uint32_t Wp, uint32_t Lx,
-                                             uint32_t Ly, uint32_t W, uint32_t n, uint32_t last_mask, uint32_t x_pbc,
-                                             uint32_t y_mode, uint32_t kxm1, uint32_t kym1, uint32_t w, int& m,
-                                             int& bb) {
-  const uint32_t row = kxm1 * Ly + kym1;
-  const size_t base = (size_t)row * Wp + w;
-  const size_t lim = (size_t)Lx * Ly * Wp;
-  const bool last = (w + 1 == W);
-  const uint32_t valid = last ? last_mask : 0xFFFFFFFFu;
-  const int nv = __popc(valid);
-  const uint32_t a = ISG_LD(A, base, lim, 21), b = ISG_LD(B, base, lim, 22);
-  m = 2 * (__popc(a & valid) + __popc(b & valid)) - 2 * nv;
-  bb = 0;
-  // +x bond
-  if (kxm1 + 1 < Lx) {
-    const size_t nb = base + (size_t)Ly * Wp;
-    bb += bonds(a, ISG_LD(A, nb, lim, 23), valid, nv) + bonds(b, ISG_LD(B, nb, lim, 24), valid, nv);
-  } else if (x_pbc) {
-    const size_t nb = base - (size_t)(Lx - 1) * Ly * Wp;
-    bb += bonds(a, ISG_LD(A, nb, lim, 25), valid, nv) + bonds(b, ISG_LD(B, nb, lim, 26), valid, nv);
+// One lattice word for measure_word, its index tested in checked builds.
+struct CheckedLoad {
+  __device__ __forceinline__ uint32_t operator()(const uint32_t* p, size_t idx, size_t lim, uint32_t site) const {
+    return ISG_LD(p, idx, lim, site);
   }
-  // +y bond
-  if (kym1 + 1 < Ly) {
-    bb += bonds(a, ISG_LD(A, base + Wp, lim, 27), valid, nv) + bonds(b, ISG_LD(B, base + Wp, lim, 28), valid, nv);
-  } else {
-    const uint32_t gkx = (y_mode == kYGapbc) ? (Lx - 1 - kxm1) : kxm1;
-    const size_t g = ((size_t)gkx * Ly) * Wp + w;
-    const int y = bonds(a, ISG_LD(A, g, lim, 29), valid, nv) + bonds(b, ISG_LD(B, g, lim, 30), valid, nv);
-    bb += (y_mode != kYPbc) ? -y : y;
-  }
-  // +z bonds: (2j, 2j+1) inside the word pair, (2j+1, 2j+2) through a shift
-  bb += bonds(a, b, valid, nv);
-  const size_t rbase = (size_t)row * Wp;
-  uint32_t an = shift_next(a, last ? ISG_LD(A, rbase, lim, 31) : ISG_LD(A, base + 1, lim, 32));
-  if (last && last_mask != 0xFFFFFFFFu) an |= (ISG_LD(A, rbase, lim, 33) & 1u) << bitpos((n - 1) & 31u);
-  bb += bonds(b, an, valid, nv);
-}
+};
 
 }  // namespace
 
@@ -822,8 +846,8 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
         if (on) {
           l = it / per;
           const uint32_t r = it - l * per, kym1 = r / W;
-          measure_word(A, B, F.Wp, Lx, Ly, W, F.n, F.last_mask, F.x_pbc, F.y_mode, kx0 + l, kym1, r - kym1 * W, m,
-                       bb);
+          measure_word(CheckedLoad{}, A, B, F.Wp, Lx, Ly, W, F.n, F.last_mask, F.x_pbc, F.y_mode, kx0 + l, kym1,
+                       r - kym1 * W, m, bb);
           bsum += bb;
         }
         const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, l, 0);
@@ -855,7 +879,7 @@ measure_partial_kernel(const FilmDesc* __restrict__ films, const uint32_t* __res
     for (uint32_t it = chunk * blockDim.x + threadIdx.x; it < Ly * W; it += bpl * blockDim.x) {
       const uint32_t kym1 = it / W, w = it % W;
       int m, bb;
-      measure_word(A, B, Wp, Lx, Ly, W, F.n, F.last_mask, F.x_pbc, F.y_mode, kxm1, kym1, w, m, bb);
+      measure_word(CheckedLoad{}, A, B, Wp, Lx, Ly, W, F.n, F.last_mask, F.x_pbc, F.y_mode, kxm1, kym1, w, m, bb);
       msum += m;
       bsum += bb;
     }
