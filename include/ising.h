@@ -300,10 +300,14 @@ int ising_batch_wait(ising_server *s, ising_ticket t, double timeout_s);
 
 /* Result of a finished job: its records (host buf, cap records of 5 + Lx
  * int64) and its final spins (host, may be NULL).  Timing in seconds since
- * the server started: submit, admit and finish.  Frees the job's slot. */
+ * the server started: submit, admit and finish.  first_chunk / last_chunk:
+ * the indices (from 0, in launch order) of the first and last chunk that ran
+ * sweeps of the job; two jobs whose ranges intersect shared launches on the
+ * device.  Frees the job's slot. */
 typedef struct {
     double t_submit, t_admit, t_finish;
     uint64_t n_records;
+    uint64_t first_chunk, last_chunk;
 } ising_job_info;
 int ising_batch_result(ising_server *s, ising_ticket t, int64_t *buf, size_t cap, int8_t *spins,
                        ising_job_info *info);

@@ -45,7 +45,12 @@ class IsingJob(_c.Structure):
 
 class IsingJobInfo(_c.Structure):
     _fields_ = [("t_submit", _c.c_double), ("t_admit", _c.c_double), ("t_finish", _c.c_double),
-                ("n_records", _c.c_uint64)]
+                ("n_records", _c.c_uint64), ("first_chunk", _c.c_uint64), ("last_chunk", _c.c_uint64)]
+
+
+class IsingSeries(_c.Structure):
+    _fields_ = [("records", P), ("n", _c.c_size_t), ("Lx", _c.c_int), ("Ly", _c.c_int), ("Lz", _c.c_int),
+                ("J", _c.c_double), ("H", _c.c_double), ("H1", _c.c_double)]
 
 
 class IsingServerStats(_c.Structure):
@@ -450,7 +455,8 @@ class Server:
                                        _c.byref(info)), "ising_batch_result")
         del self._specs[t]
         return buf[:nrec], spins, {"t_submit": info.t_submit, "t_admit": info.t_admit, "t_finish": info.t_finish,
-                                   "n_records": int(info.n_records)}
+                                   "n_records": int(info.n_records), "first_chunk": int(info.first_chunk),
+                                   "last_chunk": int(info.last_chunk)}
 
     def stats(self):
         st = IsingServerStats()

@@ -92,6 +92,7 @@ struct Job {
   ising_job p{};
   JobState state = kQueued;
   double t_submit = 0, t_admit = 0, t_finish = 0;
+  uint64_t first_chunk = 0, last_chunk = 0;  // chunks that ran its sweeps
   FilmDesc d{};  // host mirror; d.sweep = sweeps enqueued so far
   uint64_t n_records = 0;
   size_t off_spin = 0, off_rec = 0, off_part = 0, off_stage = 0;
@@ -440,6 +441,8 @@ void ising_server::loop() {
     uint64_t work = 0;
     for (ising_ticket t : films) {
       Job& j = jobs[t];
+      if (!j.inited) j.first_chunk = n_chunks;
+      j.last_chunk = n_chunks;
       j.inited = true;
       const uint32_t left = j.d.sweep_end - j.d.sweep;
       work += (uint64_t)std::min(left, chunk) * j.d.Lx * j.d.Ly * j.d.Lz;
@@ -623,6 +626,8 @@ int ising_batch_result(ising_server* s, ising_ticket t, int64_t* buf, size_t cap
     info->t_admit = j.t_admit;
     info->t_finish = j.t_finish;
     info->n_records = j.n_records;
+    info->first_chunk = j.first_chunk;
+    info->last_chunk = j.last_chunk;
   }
   s->running.erase(std::remove(s->running.begin(), s->running.end(), t), s->running.end());
   s->jobs.erase(it);

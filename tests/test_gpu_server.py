@@ -1,6 +1,8 @@
 """Continuous-batching server: every job's records and final spins equal the
 oracle's chain for that job alone, whatever else shares the device; the
 arena budget forces queueing; waits are bounded."""
+import time
+
 import numpy as np
 import pytest
 
@@ -68,4 +70,37 @@ def test_server_wait_times_out_and_rejects_oversize():
     assert e.value.status == ig.EBUSY
     srv.wait(t, 300.0)
     srv.result(t, want_spins=False)
+    srv.close()
+
+
+def test_late_job_shares_chunks_with_a_running_job():
+    """Continuous batching, not a queue: a job submitted while another is on
+    the device is admitted at the next chunk boundary and runs in the same
+    launches (their chunk ranges intersect, and it is admitted before the
+    first job finishes).  A server that ran jobs one after another would give
+    the second job a first chunk after the first job's last.  Both results
+    are still the oracle's chains for each job alone."""
+    long_job = dict(Lx=8, Ly=8, Lz=16, T=2.5, H1=0.3, seed=11, replica=0, measure_every=100, n_sweeps=20000,
+                    init_kind=ig.INIT_RANDOM, flip_p=0.0, y_mode=ig.Y_GAPBC)
+    late_job = dict(Lx=6, Ly=10, Lz=34, T=3.5, H1=0.2, seed=11, replica=1, measure_every=7, n_sweeps=300,
+                    init_kind=ig.INIT_SLAB_Y, flip_p=0.01, y_mode=ig.Y_GAPBC)
+    srv = ig.Server(64 << 20, chunk_sweeps=50)
+    (ta,) = srv.submit([long_job])
+    deadline = time.monotonic() + 60.0
+    while srv.stats()["chunks"] < 2:  # the long job is on the device
+        assert time.monotonic() < deadline
+        time.sleep(0.0005)
+    assert not srv.poll(ta)
+    (tb,) = srv.submit([late_job])
+    srv.wait(tb, 300.0)
+    srv.wait(ta, 300.0)
+    ra, sa, ia = srv.result(ta)
+    rb, sb, ib = srv.result(tb)
+    assert ib["first_chunk"] > ia["first_chunk"]
+    assert ib["first_chunk"] <= ib["last_chunk"] <= ia["last_chunk"]  # ran inside the long job's chunks
+    assert ib["t_admit"] < ia["t_finish"] and ib["t_finish"] <= ia["t_finish"]
+    for (recs, spins), sp in (((ra, sa), long_job), ((rb, sb), late_job)):
+        want_r, want_s = _oracle(sp)
+        assert np.array_equal(recs, want_r)
+        assert np.array_equal(spins, want_s)
     srv.close()
