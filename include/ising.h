@@ -463,6 +463,70 @@ int ising_critical_field(int n, const double *H1, const double *theta, double to
  * overflow); h1_star = f_s / 2 - T ln(Lx) / (2 Lz).  T, Lx, Lz > 0. */
 int ising_step_model(double H1, double f_s, double T, double Lx, double Lz, double *phi, double *h1_star);
 
+/* ------------------------------------------------- the procedures
+ * Secs. II B - IV as whole calls over the record series of a film set
+ * (each series as ising_read_series / ising_batch_read_series writes it).
+ * Records first..n-1 of every series are averaged (exact integer sums, one
+ * division).  Host memory, owned by the caller; EINVAL for null pointers,
+ * films without records past `first`, or films of one group that differ in
+ * size. */
+typedef struct {
+    const int64_t *records; /* n x (5 + Lx) int64 */
+    size_t n;
+    int Lx, Ly, Lz;
+    double J, H, H1;        /* the film's Eq. 1 couplings (for its energy) */
+} ising_series;
+
+/* Contact angle and gamma(theta) (Secs. II B, III A), for k fields H1[j]:
+ *   inter[j]  the film with the Eq. 11 boundary at H1[j];
+ *   plus[j]   a periodic-y film started all up (the (+) plateaus);
+ *   node[j * n_gl + i]  periodic-y films at the n_gl Gauss-Legendre nodes
+ *             of [0, H1[j]] (ising_gauss_legendre).
+ * inter and plus share one size.  Per field: the Eq. 17 profiles, the (-)
+ * plateaus by Eq. 12 and the dividing plane of Eq. 18 over all layers give
+ * theta[j] (and y_plus[j * Lx ...], may be NULL); the walls of the node films
+ * (per-site layer-1 and layer-Lx means) give the Young difference
+ * delta_f1[j] (Eq. 9) and Young's angle theta_young[j] (Eq. 8; NaN where
+ * |delta_f1| > gamma_pi2).  gamma[j]: Eq. 16 integrated from theta = pi/2,
+ * gamma = gamma_pi2 at H1 = 0 through the measured angles in order, with
+ * |delta_f1| (the acute angle). */
+int ising_procedure_contact_angle(int k, const double *H1, int n_gl, const ising_series *inter,
+                                  const ising_series *plus, const ising_series *node, size_t first, double gamma_pi2,
+                                  double *theta, double *theta_young, double *delta_f1, double *gamma,
+                                  double *y_plus);
+
+/* gamma(pi/2) and tau(0, pi/2) by integration over beta (Sec. II C): for
+ * n_sizes sizes Lx = Lz = L[s] and n_beta inverse temperatures beta[b]
+ * (from beta[0] < beta_c), the antiperiodic film apbc[s * n_beta + b] and
+ * the periodic film pbc[s * n_beta + b].  dF[s] = F_APBC - F_PBC at the last
+ * beta by Eq. 19 over U = <E_APBC> - <E_PBC> (Eq. 1 means), from 0 at
+ * beta[0]; then the Eq. 20 fit. */
+int ising_procedure_interface_tension(int n_sizes, const double *L, int n_beta, const double *beta,
+                                      const ising_series *apbc, const ising_series *pbc, size_t first, double *dF,
+                                      double *gamma_pi2, double *tau0);
+
+/* The line tension (Sec. IV, Eqs. 21-22) over a constant-area set of
+ * n_sizes sizes: inter[s * n_gl + i] the film with the Eq. 11 boundary and
+ * plus[s * n_gl + i] the periodic-y film at node i of [0, H1].  Per size:
+ * dF_film = the interface film's own integral over H1 (wall totals),
+ * s_wall = the (+) film's per-site integral, delta_f1 = its Young difference,
+ * and R[s] = ising_line_tension_residual with the given theta, gamma_theta
+ * and gamma_pi2; then dtau and the intercept from the scan in Lz.
+ * dF_film, s_wall, delta_f1 may be NULL. */
+int ising_procedure_line_tension(int n_sizes, int n_gl, double H1, const ising_series *inter,
+                                 const ising_series *plus, size_t first, double theta, double gamma_theta,
+                                 double gamma_pi2, double *R, double *dF_film, double *s_wall, double *delta_f1,
+                                 double *dtau, double *intercept);
+
+/* Stiffness and steps (Secs. III B, III C) from k measured angles and
+ * tensions: c and kappa (Eqs. 23-24), f_s and gamma_flat from Eq. 26 over
+ * the flat point (pi/2, gamma_pi2) and the k points, then the single-step
+ * model at that f_s for each of n_h fields H1[i]: phi[i], and h1_star
+ * (Eqs. 28-32). */
+int ising_procedure_stiffness_steps(int k, const double *theta, const double *gamma, double gamma_pi2, double T,
+                                    double Lx, double Lz, int n_h, const double *H1, double *c, double *kappa,
+                                    double *f_s, double *gamma_flat, double *phi, double *h1_star);
+
 /* ------------------------------------- measurement without allocation */
 
 /* The paper has no counterpart to this call; it exists for callers that

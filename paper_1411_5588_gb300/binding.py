@@ -129,6 +129,12 @@ _SIGS = {
     "ising_roughening_fs_fit": [_c.c_int, P, P, _c.c_double, DP, DP],
     "ising_step_model": [_c.c_double] * 5 + [DP, DP],
     "ising_critical_field": [_c.c_int, P, P] + [_c.c_double] * 4 + [DP, DP],
+    "ising_procedure_contact_angle": [_c.c_int, P, _c.c_int, P, P, P, _c.c_size_t, _c.c_double, P, P, P, P, P],
+    "ising_procedure_interface_tension": [_c.c_int, P, _c.c_int, P, P, P, _c.c_size_t, P, DP, DP],
+    "ising_procedure_line_tension": [_c.c_int, _c.c_int, _c.c_double, P, P, _c.c_size_t, _c.c_double, _c.c_double,
+                                     _c.c_double, P, P, P, P, DP, DP],
+    "ising_procedure_stiffness_steps": [_c.c_int, P, P, _c.c_double, _c.c_double, _c.c_double, _c.c_double,
+                                        _c.c_int, P, DP, DP, DP, DP, P, DP],
     "ising_measure_packed_noalloc": [P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64, P, P],
     "ising_check_counters": [_c.POINTER(_c.c_int), _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64)],
     "ising_strerror": [_c.c_int],

@@ -28,7 +28,7 @@ BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(BUILD_CHECKED, "libising_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ising_kernels.cu", "ising_api.cpp", "ising_batch.cpp", "ising_server.cpp", "ising_ti.cpp",
-           "ising_noalloc.cu", "ising_analysis.cpp", "ising_tune.cpp"]
+           "ising_noalloc.cu", "ising_analysis.cpp", "ising_procedures.cpp", "ising_tune.cpp"]
 
 
 def nvcc() -> str:

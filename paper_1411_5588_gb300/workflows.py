@@ -2,8 +2,10 @@
 
 Each procedure runs its whole film set (``workloads.*_set``) as one batch,
 meaning shared launches across films of mixed size and boundary, captured in
-CUDA graphs. It then reduces the int64 records with the library's exact
-integer means and FP64 analysis calls.
+CUDA graphs.  Its reduction is one library call over the films' record
+series (``ising_procedure_*``): the exact integer means, the per-site
+normalisations and the FP64 analysis all run there; this module only sorts
+the series by role and marshals them.
 
   contact_angle       Secs. II B, III A: theta(H1) from the dividing plane
                       (Eqs. 17-18), the Young difference (Eq. 9), Young's
@@ -16,12 +18,11 @@ integer means and FP64 analysis calls.
 """
 from __future__ import annotations
 
-import math
+import ctypes as _c
 
 import numpy as np
 
-from . import analysis as A
-from .binding import Batch, series_energy, series_mean, ti_surface_field
+from .binding import Batch, IsingSeries, check, lib
 
 
 def run(workload, use_graph=True, autotune=True):
@@ -40,92 +41,80 @@ def run(workload, use_graph=True, autotune=True):
         b.close()
 
 
-def _wall_means(rec, job, first):
-    """Per-site layer-1 and layer-Lx magnetisations (records columns 3, 4)."""
-    area = job["Ly"] * job["Lz"]
-    return series_mean(rec, 3, first) / area, series_mean(rec, 4, first) / area
+class _Series:
+    """ising_series arrays over chosen films (keeps the record arrays alive)."""
+
+    def __init__(self, records, jobs, picks):
+        self.keep = [np.ascontiguousarray(records[i], dtype=np.int64) for i in picks]
+        self.arr = (IsingSeries * max(len(picks), 1))()
+        for k, (i, r) in enumerate(zip(picks, self.keep)):
+            j = jobs[i]
+            self.arr[k] = IsingSeries(r.ctypes.data, r.shape[0], int(j["Lx"]), int(j["Ly"]), int(j["Lz"]),
+                                      float(j.get("J", 1.0)), float(j.get("H", 0.0)), float(j["H1"]))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(_c.c_void_p)
+
+
+def _index(wl):
+    return {role: i for i, role in enumerate(wl["roles"])}
 
 
 def contact_angle(wl, records, gamma_pi2):
-    first, Lx, Ly, Lz = wl["first"], wl["Lx"], wl["Ly"], wl["Lz"]
-    H1s = wl["H1s"]
-    k = len(H1s)
-    inter, plus = [None] * k, [None] * k
-    m1 = [[None] * wl["n_gl"] for _ in range(k)]
-    mn = [[None] * wl["n_gl"] for _ in range(k)]
-    for rec, job, role in zip(records, wl["jobs"], wl["roles"]):
-        if role[0] == "interface":
-            inter[role[1]] = rec
-        elif role[0] == "plus":
-            plus[role[1]] = rec
-        else:
-            m1[role[1]][role[2]], mn[role[1]][role[2]] = _wall_means(rec, job, first)
-    theta, young, delta_f1, y_plus = [], [], [], []
-    for j, h in enumerate(H1s):
-        mbar = A.layer_profile(inter[j], Lx, Ly, Lz, first)
-        m_plus = A.layer_profile(plus[j], Lx, Ly, Lz, first)
-        th, yp = A.contact_angle(Ly, mbar, m_plus, A.mirror_profile(m_plus))
-        d = A.ti_young_difference(h, m1[j], mn[j])
-        theta.append(th)
-        y_plus.append(yp)
-        delta_f1.append(d)
-        young.append(A.young_angle(d, gamma_pi2) if abs(d) <= gamma_pi2 else float("nan"))
-    # Eq. 16 from the perpendicular interface at H1 = 0
-    th_path = np.concatenate([[math.pi / 2], theta])
-    df_path = np.concatenate([[0.0], np.abs(delta_f1)])
-    gamma = A.gamma_of_theta(th_path, df_path, gamma_pi2)[1:]
-    return dict(H1=np.array(H1s), theta=np.array(theta), theta_young=np.array(young),
-                delta_f1=np.array(delta_f1), gamma=gamma, y_plus=np.array(y_plus))
+    at, k, n_gl = _index(wl), len(wl["H1s"]), wl["n_gl"]
+    inter = _Series(records, wl["jobs"], [at[("interface", j)] for j in range(k)])
+    plus = _Series(records, wl["jobs"], [at[("plus", j)] for j in range(k)])
+    node = _Series(records, wl["jobs"], [at[("node", j, i)] for j in range(k) for i in range(n_gl)])
+    H1 = _f64(wl["H1s"])
+    theta, young, delta_f1, gamma = (np.zeros(k) for _ in range(4))
+    y_plus = np.zeros((k, wl["Lx"]))
+    check(lib().ising_procedure_contact_angle(k, _p(H1), n_gl, inter.arr, plus.arr, node.arr, int(wl["first"]),
+                                              float(gamma_pi2), _p(theta), _p(young), _p(delta_f1), _p(gamma),
+                                              _p(y_plus)), "ising_procedure_contact_angle")
+    return dict(H1=H1, theta=theta, theta_young=young, delta_f1=delta_f1, gamma=gamma, y_plus=y_plus)
 
 
 def interface_tension(wl, records):
-    first, betas, sizes = wl["first"], np.asarray(wl["betas"]), wl["sizes"]
-    U = {}
-    for rec, job, role in zip(records, wl["jobs"], wl["roles"]):
-        U[role] = series_energy(rec, job["J"], job["H1"], first=first)[1]  # <E> of Eq. 1
-    dF = []
-    for s, L in enumerate(sizes):
-        dU = np.array([U[("apbc", s, k)] - U[("pbc", s, k)] for k in range(len(betas))])
-        dF.append(A.ti_free_energy_beta(betas, dU, 0.0)[-1])
-    L = np.array(sizes, dtype=np.float64)
-    gamma_pi2, tau0 = A.fit_gamma_tau(L, L, dF)
-    return dict(sizes=L, dF=np.array(dF), gamma_pi2=gamma_pi2, tau0=tau0)
+    at, sizes, betas = _index(wl), wl["sizes"], _f64(wl["betas"])
+    ns, nb = len(sizes), len(betas)
+    apbc = _Series(records, wl["jobs"], [at[("apbc", s, b)] for s in range(ns) for b in range(nb)])
+    pbc = _Series(records, wl["jobs"], [at[("pbc", s, b)] for s in range(ns) for b in range(nb)])
+    L = _f64(sizes)
+    dF = np.zeros(ns)
+    g, t = _c.c_double(), _c.c_double()
+    check(lib().ising_procedure_interface_tension(ns, _p(L), nb, _p(betas), apbc.arr, pbc.arr, int(wl["first"]),
+                                                  _p(dF), _c.byref(g), _c.byref(t)),
+          "ising_procedure_interface_tension")
+    return dict(sizes=L, dF=dF, gamma_pi2=g.value, tau0=t.value)
 
 
 def line_tension(wl, records, theta, gamma_theta, gamma_pi2):
-    first, H1, n = wl["first"], wl["H1"], wl["n_gl"]
-    sizes = wl["sizes"]
-    M1 = [[None] * n for _ in sizes]
-    Mn = [[None] * n for _ in sizes]
-    m1 = [[None] * n for _ in sizes]
-    mn = [[None] * n for _ in sizes]
-    for rec, job, role in zip(records, wl["jobs"], wl["roles"]):
-        s, i = role[1], role[2]
-        if role[0] == "interface":
-            M1[s][i], Mn[s][i] = series_mean(rec, 3, first), series_mean(rec, 4, first)
-        else:
-            m1[s][i], mn[s][i] = _wall_means(rec, job, first)
-    R, dF_film, s_wall, delta_f1 = [], [], [], []
-    for s, (Lx, Ly, Lz) in enumerate(sizes):
-        dF = ti_surface_field(H1, M1[s], Mn[s])  # totals: F_int(H1) - F_int(0)
-        sw = ti_surface_field(H1, m1[s], mn[s])  # per wall site
-        df1 = A.ti_young_difference(H1, m1[s], mn[s])
-        R.append(A.line_tension_residual(dF, Lx, Ly, Lz, theta, gamma_theta, gamma_pi2, sw, df1))
-        dF_film.append(dF)
-        s_wall.append(sw)
-        delta_f1.append(df1)
-    Lz = np.array([v[2] for v in sizes], dtype=np.float64)
-    dtau, intercept = A.line_tension_lz_scan(Lz, R)
-    return dict(Lz=Lz, R=np.array(R), dF_film=np.array(dF_film), s_wall=np.array(s_wall),
-                delta_f1=np.array(delta_f1), dtau=dtau, intercept=intercept)
+    at, ns, n_gl = _index(wl), len(wl["sizes"]), wl["n_gl"]
+    inter = _Series(records, wl["jobs"], [at[("interface", s, i)] for s in range(ns) for i in range(n_gl)])
+    plus = _Series(records, wl["jobs"], [at[("plus", s, i)] for s in range(ns) for i in range(n_gl)])
+    R, dF_film, s_wall, delta_f1 = (np.zeros(ns) for _ in range(4))
+    dtau, intercept = _c.c_double(), _c.c_double()
+    check(lib().ising_procedure_line_tension(ns, n_gl, float(wl["H1"]), inter.arr, plus.arr, int(wl["first"]),
+                                             float(theta), float(gamma_theta), float(gamma_pi2), _p(R),
+                                             _p(dF_film), _p(s_wall), _p(delta_f1), _c.byref(dtau),
+                                             _c.byref(intercept)), "ising_procedure_line_tension")
+    Lz = np.array([v[2] for v in wl["sizes"]], dtype=np.float64)
+    return dict(Lz=Lz, R=R, dF_film=dF_film, s_wall=s_wall, delta_f1=delta_f1, dtau=dtau.value,
+                intercept=intercept.value)
 
 
 def stiffness_and_steps(theta, gamma, gamma_pi2, T, Lx, Lz, H1s):
     """Eqs. 23-24 and 26 from gamma(theta); Eqs. 28-32 at the measured f_s."""
-    c, kappa = A.stiffness(theta, gamma, gamma_pi2)
-    th = np.concatenate([[math.pi / 2], theta])
-    g = np.concatenate([[gamma_pi2], gamma])
-    f_s, gamma_flat = A.step_free_energy(th, g)
-    model = [A.step_model(h, f_s, T, Lx, Lz) for h in H1s]
-    return dict(c=c, kappa=kappa, f_s=f_s, gamma_flat=gamma_flat, phi=np.array([m[0] for m in model]),
-                h1_star=model[0][1])
+    th, g, h = _f64(theta), _f64(gamma), _f64(H1s)
+    phi = np.zeros(h.size)
+    c, kappa, f_s, flat, h1s = (_c.c_double() for _ in range(5))
+    check(lib().ising_procedure_stiffness_steps(th.size, _p(th), _p(g), float(gamma_pi2), float(T), float(Lx),
+                                                float(Lz), h.size, _p(h), _c.byref(c), _c.byref(kappa),
+                                                _c.byref(f_s), _c.byref(flat), _p(phi), _c.byref(h1s)),
+          "ising_procedure_stiffness_steps")
+    return dict(c=c.value, kappa=kappa.value, f_s=f_s.value, gamma_flat=flat.value, phi=phi, h1_star=h1s.value)
