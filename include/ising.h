@@ -546,17 +546,21 @@ int ising_procedure_stiffness_steps(int k, const double *theta, const double *ga
  * The per-block partial sums go to one fixed 128 KiB device array inside the
  * library (16384 int64), so the film may use at most 8192 measurement blocks,
  * Lx * ceil(Ly * ceil(Lz / 64) / 1024) <= 8192; larger films get EINVAL.
- * The first call on each device looks up that array's device address (do it
- * before any stream capture).  All calls on a device share the array: each
- * call overwrites every partial it reads, so nothing needs clearing, but
- * calls whose kernels overlap on the GPU race on it. */
+ * Each call looks up that array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a device
+ * may load the library's device code there, so make it before any stream
+ * capture.  All calls on a device share the array: each call overwrites
+ * every partial it reads, so nothing needs clearing, but calls whose kernels
+ * overlap on the GPU race on it -- serialise them on one stream or order
+ * them with events. */
 int ising_measure_packed_noalloc(const uint32_t *spins, int Lx, int Ly, int Lz, int y_mode, int x_mode,
                                  uint64_t sweep, int64_t *record, void *stream);
 
 /* ------------------------------------------------------------- misc */
 
 /* Bounds checking.  A library built with ISING_CHECKED tests every lattice
- * word index of the update, resident and record kernels against its plane:
+ * word index of the update, resident and record kernels (and of
+ * ising_measure_packed_noalloc) against its plane:
  * an out-of-range index is counted and the first one kept (site id << 48 |
  * index), and the access is redirected (a load reads word 0, a store is
  * dropped) -- nothing traps.  *checked = 1 for such a build, with the totals

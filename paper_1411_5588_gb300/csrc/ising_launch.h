@@ -101,6 +101,8 @@ cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_byt
 // Checked builds: the out-of-range access counters (returns 1); other
 // builds return 0 with both zero; -1 on a CUDA error.
 int read_oob_counters(unsigned long long* count, unsigned long long* first);
+// The same for the allocation-free measurement kernel (ising_noalloc.cu).
+int read_noalloc_oob_counters(unsigned long long* count, unsigned long long* first);
 int update_blocks_per_sm();
 int measure_blocks_per_sm();
 

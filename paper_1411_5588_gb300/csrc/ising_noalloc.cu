@@ -19,7 +19,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "ising_host.h"
 
@@ -46,12 +45,33 @@ __device__ __forceinline__ int64_t na_block_sum(int64_t v, int64_t* s_red) {
   return t;
 }
 
-__device__ __forceinline__ int na_bonds(uint32_t a, uint32_t b, uint32_t valid, int nv) {
-  return nv - 2 * __popc((a ^ b) & valid);
-}
+// Checked builds (-DISING_CHECKED) count out-of-range word indices of this
+// file's kernel the way the other kernels do (ising_check_counters adds them
+// in): the first one is kept and the access reads word 0 instead.
+#ifdef ISING_CHECKED
+__device__ unsigned long long g_na_oob_count;
+__device__ unsigned long long g_na_oob_first;
+#endif
+
+struct NaLoad {
+  __device__ __forceinline__ uint32_t operator()(const uint32_t* p, size_t idx, size_t lim, uint32_t site) const {
+#ifdef ISING_CHECKED
+    if (idx >= lim) {
+      atomicAdd(&g_na_oob_count, 1ull);
+      atomicCAS(&g_na_oob_first, 0ull, ((unsigned long long)site << 48) | (idx & 0xFFFFFFFFFFFFull));
+      return p[0];
+    }
+#else
+    (void)lim;
+    (void)site;
+#endif
+    return p[idx];
+  }
+};
 
 // First pass: block (layer kx, chunk c) sums m and the +x/+y/+z bonds of its
-// rows into part[2 * (kx * bpl + c) + {0, 1}].
+// rows (measure_word, the record arithmetic every measurement kernel shares)
+// into part[2 * (kx * bpl + c) + {0, 1}].
 __global__ void __launch_bounds__(kNaBlock)
 na_partial_kernel(const __grid_constant__ FilmDesc F, const uint32_t* __restrict__ spins,
                   int64_t* __restrict__ part) {
@@ -60,38 +80,11 @@ na_partial_kernel(const __grid_constant__ FilmDesc F, const uint32_t* __restrict
   const uint32_t kxm1 = blockIdx.x / bpl, chunk = blockIdx.x % bpl;
   const uint32_t* A = spins;
   const uint32_t* B = A + (size_t)Lx * Ly * Wp;
-  const bool neg = F.y_mode != kYPbc;
-  const uint32_t gkx = (F.y_mode == kYGapbc) ? (Lx - 1 - kxm1) : kxm1;
   int64_t msum = 0, bsum = 0;
   for (uint32_t it = chunk * blockDim.x + threadIdx.x; it < Ly * W; it += bpl * blockDim.x) {
     const uint32_t kym1 = it / W, w = it % W;
-    const uint32_t row = kxm1 * Ly + kym1;
-    const size_t base = (size_t)row * Wp + w;
-    const bool last = (w + 1 == W);
-    const uint32_t valid = last ? F.last_mask : 0xFFFFFFFFu;
-    const int nv = __popc(valid);
-    const uint32_t a = A[base], b = B[base];
-    const int m = 2 * (__popc(a & valid) + __popc(b & valid)) - 2 * nv;
-    int bb = 0;
-    if (kxm1 + 1 < Lx) {
-      const size_t nb = base + (size_t)Ly * Wp;
-      bb += na_bonds(a, A[nb], valid, nv) + na_bonds(b, B[nb], valid, nv);
-    } else if (F.x_pbc) {
-      const size_t nb = base - (size_t)(Lx - 1) * Ly * Wp;
-      bb += na_bonds(a, A[nb], valid, nv) + na_bonds(b, B[nb], valid, nv);
-    }
-    if (kym1 + 1 < Ly) {
-      bb += na_bonds(a, A[base + Wp], valid, nv) + na_bonds(b, B[base + Wp], valid, nv);
-    } else {
-      const size_t g = ((size_t)gkx * Ly) * Wp + w;
-      const int y = na_bonds(a, A[g], valid, nv) + na_bonds(b, B[g], valid, nv);
-      bb += neg ? -y : y;
-    }
-    bb += na_bonds(a, b, valid, nv);
-    const size_t rbase = (size_t)row * Wp;
-    uint32_t an = shift_next(a, last ? A[rbase] : A[base + 1]);
-    if (last && F.last_mask != 0xFFFFFFFFu) an |= (A[rbase] & 1u) << bitpos((F.n - 1) & 31u);
-    bb += na_bonds(b, an, valid, nv);
+    int m, bb;
+    measure_word(NaLoad{}, A, B, Wp, Lx, Ly, W, F.n, F.last_mask, F.x_pbc, F.y_mode, kxm1, kym1, w, m, bb);
     msum += m;
     bsum += bb;
   }
@@ -131,27 +124,32 @@ na_finalize_kernel(const __grid_constant__ FilmDesc F, const int64_t* __restrict
   }
 }
 
-// Device address of the scratch array, looked up once per device.
-constexpr int kMaxDevices = 64;
-std::mutex g_na_mu;
-int64_t* g_na_ptr[kMaxDevices] = {};
-
+// Device address of the scratch array on the current device.  Host code
+// sees only a stand-in for the symbol, so the address is looked up on every
+// call (no allocation; the runtime keeps it per loaded module), which also
+// stays right after a device reset reloads the module.
 int noalloc_scratch(int64_t** out) {
-  int dev = 0;
-  ISG_CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(ISING_EINVAL, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lk(g_na_mu);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return fail(ISING_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_na_ptr[dev] = static_cast<int64_t*>(p);
-  }
-  *out = g_na_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return fail(ISING_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  *out = static_cast<int64_t*>(p);
   return ISING_OK;
 }
 
 }  // namespace
+
+int read_noalloc_oob_counters(unsigned long long* count, unsigned long long* first) {
+#ifdef ISING_CHECKED
+  if (cudaMemcpyFromSymbol(count, g_na_oob_count, sizeof *count) != cudaSuccess) return -1;
+  if (cudaMemcpyFromSymbol(first, g_na_oob_first, sizeof *first) != cudaSuccess) return -1;
+  return 1;
+#else
+  *count = 0;
+  *first = 0;
+  return 0;
+#endif
+}
+
 }  // namespace isg
 
 using namespace isg;

@@ -1,5 +1,6 @@
 """The library built with ISING_CHECKED (every lattice word index of the
-update, resident and record kernels tested against its plane): all parity
+update, resident and record kernels and of the allocation-free measurement
+tested against its plane): all parity
 shapes and a set of random films, every launch shape, bit-identical to the
 oracle, and not one out-of-range access.  Runs in a child process, because a
 process loads one build of the library."""
@@ -41,6 +42,24 @@ for shape in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q):
     b.set_shape(shape)
     b.sweep(4, False)
 b.close()
+# the allocation-free measurement (its own kernel, the same record code)
+import ctypes
+import torch
+for Lx, Ly, Lz, ym, xm in ((24, 32, 130, 0, 0), (12, 18, 70, 2, 1), (8, 256, 512, 1, 0), (7, 9, 2, 0, 0)):
+    g = ig.Film(Lx, Ly, Lz, 1.0, 0.45, 2.8, 13, y_mode=ym, x_mode=xm)
+    g.init(ig.INIT_SLAB_Y, 0.05)
+    g.sweep(3, 0)
+    packed = torch.empty(g.packed_words(), dtype=torch.int32, device="cuda")
+    rec = torch.zeros(5 + Lx, dtype=torch.int64, device="cuda")
+    g.get_packed_device(packed.data_ptr())
+    g.synchronize()
+    ig.check(ig.lib().ising_measure_packed_noalloc(ctypes.c_void_p(packed.data_ptr()), Lx, Ly, Lz, ym, xm,
+                                                   g.sweep_count, ctypes.c_void_p(rec.data_ptr()), None),
+             "ising_measure_packed_noalloc")
+    torch.cuda.synchronize()
+    assert np.array_equal(rec.cpu().numpy(), g.measure()), (Lx, Ly, Lz)
+    g.close()
+    films += 1
 checked, count, first = ig.check_counters()
 print(json.dumps({"checked": checked, "count": count, "first": first, "films": films}))
 """
