@@ -414,10 +414,75 @@ def procedures(ig, WL):
     r_lt = PW.line_tension(lt, recs, r_ca["theta"][j], r_ca["gamma"][j], r_it["gamma_pi2"])
     out["line_tension"] = {"sizes": [list(v) for v in lt["sizes"]], "H1": lt["H1"], "R": r_lt["R"].tolist(),
                            "dtau": r_lt["dtau"], "intercept": r_lt["intercept"], "host_s": time.perf_counter() - t0}
+    out["physics_note"] = ("not converged: a throughput leg (2000 sweeps, 500 discarded, sizes scaled down from "
+                           "the paper's); its physics values are not estimates of the paper's quantities")
     runs = [out[k] for k in ("interface_tension_run", "contact_angle_run", "line_tension_run")]
     out["attempts_per_ns"] = sum(r["attempts"] for r in runs) / sum(r["sweep_s"] for r in runs) / 1e9
     out["unit"] = UNIT
     return out
+
+
+PROFILE_SETS = ("ti64", "contact_angle", "interface_tension", "line_tension")
+
+
+def profile_set(args):
+    """--profile-set: one film set as a batch for a few sweeps in a fixed
+    launch shape, records after every sweep unless --profile-every says
+    otherwise (0: none), in one lane unless --profile-lanes says otherwise (so
+    that one launch covers the whole set).  The command the batch kernels'
+    ncu summaries in profiles/ are captured from; it prints one summary line,
+    not a benchmark line."""
+    import paper_1411_5588_gb300 as ig
+    from paper_1411_5588_gb300 import workloads as WL
+    n = args.profile_sweeps
+    jobs = {"ti64": lambda: WL.ti_batch(n_sweeps=n),
+            "contact_angle": lambda: WL.contact_angle_set(n_sweeps=n)["jobs"],
+            "interface_tension": lambda: WL.interface_tension_set(n_sweeps=n)["jobs"],
+            "line_tension": lambda: WL.line_tension_set(n_sweeps=n)["jobs"]}[args.profile_set]()
+    if args.profile_every is not None:
+        jobs = [dict(j, measure_every=args.profile_every) for j in jobs]
+    b = ig.Batch(jobs, lanes=args.profile_lanes)
+    b.set_shape({"grid1": ig.SHAPE_GRID_1, "grid2": ig.SHAPE_GRID_2, "gridq": ig.SHAPE_GRID_Q}[args.profile_shape])
+    if args.profile_every != 0:
+        b.reserve_records(n)
+    b.sweep(n, False)
+    b.synchronize()
+    lanes = b.lanes
+    b.close()
+    print(f"{args.profile_set}: {len(jobs)} films in {lanes} lane(s), {n} sweeps, shape {args.profile_shape}, "
+          f"records every {jobs[0]['measure_every']} sweeps")
+
+
+def headline(extras):
+    """The side legs' figures in short, last on the JSON line."""
+    h = {}
+    b = extras.get("batched") or {}
+    if "ratio" in b:
+        h["batched_64_films"] = {"batched": round(b["batched"], 1), "plain": round(b["plain"], 1),
+                                 "ratio": round(b["ratio"], 2), "alu_frac": round(b["batched_alu_frac"], 3)}
+    s = extras.get("serving") or {}
+    if "p50_latency_s" in s:
+        h["serving_2000_jobs"] = {"attempts_per_ns": round(s["attempts_per_ns"], 1),
+                                  "offered_attempts_per_ns": round(s["offered_attempts_per_ns"], 1),
+                                  "p50_ms": round(1e3 * s["p50_latency_s"], 1),
+                                  "p99_ms": round(1e3 * s["p99_latency_s"], 1)}
+    c = extras.get("serving_capacity") or {}
+    if "ratio" in c:
+        h["served_vs_plain"] = {"served": round(c["served"], 1), "plain": round(c["plain"], 1),
+                                "ratio": round(c["ratio"], 2)}
+    p = extras.get("procedures") or {}
+    for k in ("interface_tension_run", "contact_angle_run", "line_tension_run"):
+        if k in p:
+            h[k.replace("_run", "_set")] = {"attempts_per_ns": round(p[k]["attempts_per_ns"], 1),
+                                           "alu_frac": round(p[k]["alu_frac"], 3)}
+    t = extras.get("t_scan") or {}
+    if "attempts_per_ns" in t:
+        h["t_scan_40_films"] = {"attempts_per_ns": round(t["attempts_per_ns"], 1), "alu_frac": round(t["alu_frac"], 3)}
+    f = extras.get("film_8") or {}
+    if "attempts_per_ns" in f:
+        h["film_8"] = {"attempts_per_ns": round(f["attempts_per_ns"], 3)}
+    h["unit"] = UNIT
+    return h
 
 
 def main():
@@ -431,7 +496,16 @@ def main():
     ap.add_argument("--shape", default="auto", choices=["auto", "grid1", "grid2"],
                     help="launch shape of the 120x240x1600 film (auto: the library's autotuner); profiling "
                          "pins the autotuner's normal pick because ncu's serialisation distorts its timing")
+    ap.add_argument("--profile-set", choices=PROFILE_SETS,
+                    help="run one film set for ncu (see profile_set) instead of the benchmark")
+    ap.add_argument("--profile-shape", default="grid2", choices=["grid1", "grid2", "gridq"])
+    ap.add_argument("--profile-sweeps", type=int, default=4)
+    ap.add_argument("--profile-every", type=int, default=None, help="record interval (0: no records)")
+    ap.add_argument("--profile-lanes", type=int, default=1, help="batch lanes (0: the library's default)")
     args = ap.parse_args()
+    if args.profile_set:
+        profile_set(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -576,6 +650,8 @@ def main():
             "roofline": roofline, "clocks": clocks, "gpu_launches": per_step_launches * args.steps,
             "e2e": e2e, "cpu_baseline": cpu}
     line.update(extras)
+    if extras:
+        line["headline"] = headline(extras)  # last, so that a cut-off tail still shows it
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
