@@ -173,6 +173,83 @@ struct PhiloxRow {
   }
 };
 
+// The same calls with one more product hoisted: round 2's word 0 does not
+// depend on c1 either, so neither does round 3's product of it.  Each call
+// then starts at round 2 with one product there and one in round 3 (16 wide
+// multiplies per call instead of 17).  It keeps two more words live across
+// the calls, which the single-film kernel has room for.
+struct PhiloxRow3 {
+  uint32_t r1_hi1, r1_c3;  // round 1: hi(M1 * sweep) (x0 before the c1 and key xor), x3
+  uint32_t r2_c1;          // round 2: y1
+  uint32_t r3_x2, r3_c3;   // round 3: hi(M0 * y0) ^ key (z2 before the y3 xor), z3
+  const uint32_t* rk0;
+  const uint32_t* rk1;
+  __device__ __forceinline__ PhiloxRow3(uint32_t row, uint32_t sweep, uint32_t parity, const uint32_t* k0,
+                                       const uint32_t* k1)
+      : rk0(k0), rk1(k1) {
+    // round 1 with counter (row, c1, sweep, parity)
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * row, p1 = (uint64_t)kPhiloxM1 * sweep;
+    r1_hi1 = (uint32_t)(p1 >> 32);
+    const uint32_t x1 = (uint32_t)p1;
+    const uint32_t x2 = (uint32_t)(p0 >> 32) ^ parity ^ rk1[0];
+    r1_c3 = (uint32_t)p0;
+    // round 2: word 0 and word 1 come from the product of x2
+    const uint64_t q1 = (uint64_t)kPhiloxM1 * x2;
+    const uint32_t y0 = (uint32_t)(q1 >> 32) ^ x1 ^ rk0[1];
+    r2_c1 = (uint32_t)q1;
+    // round 3: the product of y0
+    const uint64_t q0 = (uint64_t)kPhiloxM0 * y0;
+    r3_x2 = (uint32_t)(q0 >> 32) ^ rk1[2];
+    r3_c3 = (uint32_t)q0;
+  }
+  // Rounds 2 and 3 of the call with counter word 1 = c1: (z0, z1, z2, z3).
+  __device__ __forceinline__ void head(uint32_t c1, uint32_t& z0, uint32_t& z1, uint32_t& z2, uint32_t& z3) const {
+    const uint32_t x0 = r1_hi1 ^ c1 ^ rk0[0];  // end of round 1
+    const uint64_t pp = (uint64_t)kPhiloxM0 * x0;
+    const uint32_t y2 = (uint32_t)(pp >> 32) ^ r1_c3 ^ rk1[1], y3 = (uint32_t)pp;
+    const uint64_t qq = (uint64_t)kPhiloxM1 * y2;
+    z0 = (uint32_t)(qq >> 32) ^ r2_c1 ^ rk0[2];
+    z1 = (uint32_t)qq;
+    z2 = r3_x2 ^ y3;
+    z3 = r3_c3;
+  }
+  // Full Philox4x32-10 output for counter word 1 = c1.
+  __device__ __forceinline__ void draw(uint32_t c1, uint32_t out[4]) const {
+    uint32_t c0, c1w, c2, c3;
+    head(c1, c0, c1w, c2, c3);
+#pragma unroll
+    for (int r = 3; r < 10; r++) {
+      const uint64_t p0 = (uint64_t)kPhiloxM0 * c0, p1 = (uint64_t)kPhiloxM1 * c2;
+      c0 = (uint32_t)(p1 >> 32) ^ c1w ^ rk0[r];
+      c1w = (uint32_t)p1;
+      c2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+      c3 = (uint32_t)p0;
+    }
+    out[0] = c0; out[1] = c1w; out[2] = c2; out[3] = c3;
+  }
+  // Two Philox calls (counter words 1 = c1a and c1b) computed side by side.
+  __device__ __forceinline__ void draw2(uint32_t c1a, uint32_t c1b, uint32_t oa[4], uint32_t ob[4]) const {
+    uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+    head(c1a, a0, a1, a2, a3);
+    head(c1b, b0, b1, b2, b3);
+#pragma unroll
+    for (int r = 3; r < 10; r++) {
+      const uint64_t pa0 = (uint64_t)kPhiloxM0 * a0, pa1 = (uint64_t)kPhiloxM1 * a2;
+      const uint64_t pb0 = (uint64_t)kPhiloxM0 * b0, pb1 = (uint64_t)kPhiloxM1 * b2;
+      a0 = (uint32_t)(pa1 >> 32) ^ a1 ^ rk0[r];
+      a1 = (uint32_t)pa1;
+      a2 = (uint32_t)(pa0 >> 32) ^ a3 ^ rk1[r];
+      a3 = (uint32_t)pa0;
+      b0 = (uint32_t)(pb1 >> 32) ^ b1 ^ rk0[r];
+      b1 = (uint32_t)pb1;
+      b2 = (uint32_t)(pb0 >> 32) ^ b3 ^ rk1[r];
+      b3 = (uint32_t)pb0;
+    }
+    oa[0] = a0; oa[1] = a1; oa[2] = a2; oa[3] = a3;
+    ob[0] = b0; ob[1] = b1; ob[2] = b2; ob[3] = b3;
+  }
+};
+
 // Word whose local site l holds site l-1 of the array (z-1 neighbour of
 // parity-0 sites), `prev` being the word before (its bit 31 = local site 31).
 __device__ __forceinline__ uint32_t shift_prev(uint32_t v, uint32_t prev) {

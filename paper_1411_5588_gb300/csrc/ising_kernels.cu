@@ -381,7 +381,7 @@ __device__ __forceinline__ uint32_t FilmCtx::path() const {
   return last_calls <= 4 ? kSingle : kPartial;
 }
 
-template <uint32_t PATH, bool FAST, bool QUARTER, bool MEAS = false>
+template <uint32_t PATH, bool FAST, bool QUARTER, bool MEAS = false, bool H3 = false>
 __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched& f,
                                                 const uint32_t* __restrict__ s_thr,
                                                 const uint32_t* __restrict__ s_alw, uint32_t qsel,
@@ -451,7 +451,8 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
   const uint32_t ncalls = FULL ? 8u : PATH == kMixed ? (partial ? c.last_calls : 8u) : c.last_calls;
   const uint32_t clsb = (cls * 64u) * 0x01010101u;  // byte offset of this class's table
   const char* tb = reinterpret_cast<const char*>(s_thr);
-  const PhiloxRow pr(row, c.sweep, X, c.rk0, c.rk1);
+  using Row = typename std::conditional<H3, PhiloxRow3, PhiloxRow>::type;
+  const Row pr(row, c.sweep, X, c.rk0, c.rk1);
   uint32_t lt = 0;
   // calls Q and Q + 4 are drawn together (two independent Philox chains),
   // except on the kSingle path
@@ -522,19 +523,20 @@ __device__ __forceinline__ uint32_t decide_word(const FilmCtx& c, const Fetched&
 // warp).  PATHS4 = false keeps two bodies only (for the kernel whose register
 // budget has no room for more): full words on kFull, a partial last word on
 // kPartial, chosen per word.
-template <bool FAST, bool QUARTER, bool MEAS, bool PATHS4>
+template <bool FAST, bool QUARTER, bool MEAS, bool PATHS4, bool H3 = false>
 __device__ __forceinline__ uint32_t decide_any(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
                                                const uint32_t* s_alw, uint32_t qsel, uint32_t* stash) {
   if (!PATHS4) {
     if (f.w + 1 < c.W || c.last_mask == 0xFFFFFFFFu)
-      return decide_word<kFull, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
-    return decide_word<kPartial, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+      return decide_word<kFull, FAST, QUARTER, MEAS, H3>(c, f, s_thr, s_alw, qsel, stash);
+    return decide_word<kPartial, FAST, QUARTER, MEAS, H3>(c, f, s_thr, s_alw, qsel, stash);
   }
   const uint32_t path = c.path();
-  if (path == kFull) return decide_word<kFull, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
-  if (path == kMixed) return decide_word<kMixed, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
-  if (!QUARTER && path == kSingle) return decide_word<kSingle, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
-  return decide_word<kPartial, FAST, QUARTER, MEAS>(c, f, s_thr, s_alw, qsel, stash);
+  if (path == kFull) return decide_word<kFull, FAST, QUARTER, MEAS, H3>(c, f, s_thr, s_alw, qsel, stash);
+  if (path == kMixed) return decide_word<kMixed, FAST, QUARTER, MEAS, H3>(c, f, s_thr, s_alw, qsel, stash);
+  if (!QUARTER && path == kSingle)
+    return decide_word<kSingle, FAST, QUARTER, MEAS, H3>(c, f, s_thr, s_alw, qsel, stash);
+  return decide_word<kPartial, FAST, QUARTER, MEAS, H3>(c, f, s_thr, s_alw, qsel, stash);
 }
 
 __device__ __forceinline__ void store_word(const FilmCtx& c, const Fetched& f, uint32_t v) {
@@ -563,11 +565,11 @@ __device__ __forceinline__ void item_word(const FilmCtx& c, uint32_t item, uint3
 
 // MEAS: also return the record sums of the word (r1) and of its partner word
 // (r2, ky = 1 only), using the thread's stash slots.
-template <bool FAST, bool MEAS = false, bool PATHS4 = true>
+template <bool FAST, bool MEAS = false, bool PATHS4 = true, bool H3 = false>
 __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& f, const uint32_t* s_thr,
                                                const uint32_t* s_alw, uint32_t* stash = nullptr,
                                                LayerSums* r1 = nullptr, LayerSums* r2 = nullptr) {
-  const uint32_t fl = decide_any<FAST, false, MEAS, PATHS4>(c, f, s_thr, s_alw, 0, stash);
+  const uint32_t fl = decide_any<FAST, false, MEAS, PATHS4, H3>(c, f, s_thr, s_alw, 0, stash);
   const uint32_t v = f.S ^ fl;
   store_word(c, f, v);
   if (MEAS) *r1 = word_sums(c, f.kx, f.w, fl, v, stash);
@@ -578,7 +580,7 @@ __device__ __forceinline__ void update_fetched(const FilmCtx& c, const Fetched& 
     Fetched g;
     fetch_word(c, kx2, c.Ly, f.w, g);
     if (MEAS) stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3], g) : 0u;
-    const uint32_t fl2 = decide_any<FAST, false, MEAS, PATHS4>(c, g, s_thr, s_alw, 0, stash);
+    const uint32_t fl2 = decide_any<FAST, false, MEAS, PATHS4, H3>(c, g, s_thr, s_alw, 0, stash);
     const uint32_t v2 = g.S ^ fl2;
     store_word(c, g, v2);
     if (MEAS) {
@@ -633,7 +635,7 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
 // sums go into the film's per-layer accumulators acc_of() (a pointer made
 // where it is used, not kept across the draws); s_stash holds kStashSlots
 // words per thread.
-template <bool FAST, uint32_t ITEMS, bool MEAS, bool PATHS4, typename AccOf>
+template <bool FAST, uint32_t ITEMS, bool MEAS, bool PATHS4, bool H3, typename AccOf>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw,
@@ -676,7 +678,7 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 #pragma unroll
     for (uint32_t it = 0; it < NI; it++) {
       LayerSums r1, r2;
-      if (mine[it]) update_fetched<FAST, true, PATHS4>(c, fw[it], s_thr, s_alw, stash, &r1, &r2);
+      if (mine[it]) update_fetched<FAST, true, PATHS4, H3>(c, fw[it], s_thr, s_alw, stash, &r1, &r2);
       add_layer_sums(acc_of(), r1);
       add_lane_sums(acc_of(), r2);
     }
@@ -684,7 +686,7 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
   }
 #pragma unroll
   for (uint32_t it = 0; it < NI; it++)
-    if (mine[it]) update_fetched<FAST, false, PATHS4>(c, fw[it], s_thr, s_alw);
+    if (mine[it]) update_fetched<FAST, false, PATHS4, H3>(c, fw[it], s_thr, s_alw);
 }
 
 // Half-sweep of every film of a launch: block b handles words_per_block(ITEMS)
@@ -762,7 +764,7 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     const uint32_t first = (vb - s_d.upd_block_begin) * words_per_block(ITEMS);
     // two words per thread, and the exact table: the register budget keeps
     // the two-path decision
-    sweep_block<FAST, ITEMS, MEAS, FAST && ITEMS != 2>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
+    sweep_block<FAST, ITEMS, MEAS, FAST && ITEMS != 2, false>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
                                    s_alw, meas, acc_of, s_stash);
   }
 }
@@ -797,7 +799,9 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   c.plane1 = c.plane0 + (size_t)d.Lx * d.Ly * d.Wp;
   c.seam_same = seam_joins_one_colour(d.Lx, d.Ly, d.y_mode);
   auto acc_of = [acc]() { return reinterpret_cast<unsigned long long*>(acc); };
-  sweep_block<FAST, ITEMS, MEAS, true>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
+  // the Philox head with round 3's product hoisted (PhiloxRow3) wherever the
+  // registers allow it: not in the recording launch
+  sweep_block<FAST, ITEMS, MEAS, true, !MEAS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
                                  d.divy_l, s_thr, s_alw, MEAS, acc_of, s_stash);
 }
 
