@@ -81,6 +81,19 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   d.sweep_end = 0xFFFFFFFFu;
   fastdiv_magic(d.W, &d.divw_m, &d.divw_l);
   fastdiv_magic(d.Ly > 2 ? d.Ly - 2 : 1, &d.divy_m, &d.divy_l);  // rows ky = 2 .. Ly-1 of a layer
+  // thin films: the one-word grid kernels update 4 (at most 8 sites per
+  // array) or 2 (at most 16) rows per packed word; the first and the last
+  // group of a layer must differ.  Two rows pay only on films of at least
+  // kPack2Rows rows: packing halves a film's threads and doubles each one's
+  // chain of Philox calls, which a small film's few waves cannot hide
+  // (measured on GB300: the beta-integration set's films of 1200-3000 rows
+  // lose 6%, the line-tension set's of 13824 rows gain)
+  d.pack = 1;
+  if (d.W == 1 && d.n <= 8 && d.Ly % 4 == 0 && d.Ly >= 8) d.pack = 4;
+  else if (d.W == 1 && d.n <= 16 && d.Ly % 2 == 0 && d.Ly >= 4 && d.Lx * d.Ly >= kPack2Rows) d.pack = 2;
+  const uint32_t groups = d.Ly / d.pack;
+  d.pk_items = d.Lx * (groups - 1);
+  fastdiv_magic(groups > 2 ? groups - 2 : 1, &d.pk_divm, &d.pk_divl);
 }
 
 void build_tables(FilmDesc& d, double J, double H, double H1, double T) {
@@ -143,7 +156,7 @@ void FilmSet::layout(bool assign_part) {
     d.upd_block_begin = ub;
     d.meas_block_begin = mb;
     if (assign_part) d.part_off = po;
-    ub += (d.upd_items + words_per_block(items) - 1) / words_per_block(items);
+    ub += (grid_items(d, items) + words_per_block(items) - 1) / words_per_block(items);
     mb += meas_units(d);
     po += part_len(d);
   }
@@ -176,7 +189,7 @@ int FilmSet::upload() {
   uint32_t* om = ou + hh.upd_blocks;
   for (size_t f = 0; f < nf; f++) {
     const FilmDesc& d = h[f];
-    const uint32_t nb = (d.upd_items + words_per_block(items) - 1) / words_per_block(items);
+    const uint32_t nb = (grid_items(d, items) + words_per_block(items) - 1) / words_per_block(items);
     for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
     for (uint32_t b = 0; b < meas_units(d); b++) om[d.meas_block_begin + b] = (uint32_t)f;
   }
@@ -196,8 +209,11 @@ uint32_t FilmSet::fin_grid() const { return std::min<uint32_t>(hh.n_films, (uint
 int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_grid) {
   const uint32_t ug = fixed_grid ? upd_grid_max() : upd_grid();
   const uint32_t fg = fixed_grid ? (uint32_t)(2 * n_sm) : fin_grid();
-  bool exact = false;
-  for (const auto& d : h) exact = exact || (d.active && d.has_never);
+  bool exact = false, pack = false;
+  for (const auto& d : h) {
+    exact = exact || (d.active && d.has_never);
+    pack = pack || d.pack > 1;
+  }
   bool prev_meas = false;
   for (uint32_t k = k0; k < k0 + n; k++) {
     bool meas = all_meas;
@@ -210,8 +226,8 @@ int FilmSet::enqueue_sweeps(uint32_t k0, uint32_t n, bool all_meas, bool fixed_g
         }
     // records: half-sweep 1 accumulates the sums; the next half-sweep 0
     // writes them, or, after the last sweep of the call, a small kernel
-    ISG_CK(launch_update(L, ug, pool, 0, k, exact, items, part, rec, false, prev_meas ? k : 0, stream));
-    ISG_CK(launch_update(L, ug, pool, 1, k, exact, items, part, rec, meas, 0, stream));
+    ISG_CK(launch_update(L, ug, pool, 0, k, exact, items, pack, part, rec, false, prev_meas ? k : 0, stream));
+    ISG_CK(launch_update(L, ug, pool, 1, k, exact, items, pack, part, rec, meas, 0, stream));
     if (meas && k + 1 == k0 + n) ISG_CK(launch_record(L, fg, part, rec, k + 1, stream));
     prev_meas = meas;
   }

@@ -58,7 +58,9 @@ struct FilmDesc {
   uint32_t has_never;          // some reachable entry has dE > 0 and thr = 0
   uint32_t meas_lpu;           // layers per measurement block (> 1 only when meas_bpl = 1)
   uint32_t rk0[10], rk1[10];   // Philox round keys: key + r * Weyl constant
-  uint32_t reserved2[4];
+  uint32_t pack;               // rows per packed word in the one- and two-word grid kernels (1, 2, 4)
+  uint32_t pk_items;           // their items when pack > 1: Lx * (Ly / pack - 1) groups of pack rows
+  uint32_t pk_divm, pk_divl;   // division by Ly / pack - 2 (by 1 when that is 0)
 };
 
 // Division by a runtime constant d < 2^31 for numerators n < 2^31 (round-up

@@ -121,6 +121,7 @@ struct FilmCtx {
   uint32_t Lx, Ly, n, W, Wp, y_mode, x_pbc, last_mask, last_calls;
   uint32_t plane_words;  // words of one plane (Lx * Ly * Wp), for checked builds
   uint32_t seam_same;    // the y-wrap bonds join sites of one colour (Lx+Ly even under Eq. 11, Ly odd otherwise)
+  uint32_t pack;         // rows per packed word (1, 2 or 4) in the grid kernels' items
   // decision path of the film's words (kFull, kPartial, kSingle or kMixed)
   __device__ __forceinline__ uint32_t path() const;
   const uint32_t* rk0;  // Philox round keys (constant bank or shared memory)
@@ -626,6 +627,321 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
   }
 }
 
+// ---- thin films: several rows per register
+//
+// A film whose rows hold one partial word per parity array (W = 1) with at
+// most 8 sites (R = 4) or 16 sites (R = 2) per array spends the per-word work
+// -- neighbour count, table indices, stores -- on a quarter or a half of a
+// word's 32 sites.  The grid kernels then update R rows (kx, ky0 .. ky0+R-1)
+// of one layer at once: row j's bits, which sit in the low B = 8/R bits of
+// each byte, move up by j*B bits into one register, and the decision runs
+// once on the packed word.  Packed bit j*B + q + 8*I is row j's site
+// 4q + I, served by that row's Philox call q: the bit-to-call rule of a full
+// word holds with "call" Q = j*B + q and the row's own counter.  The
+// checkerboard is unchanged: consecutive rows update opposite arrays, and
+// none reads an array another updates in the same half-sweep.  The memory
+// layout is the same as for every other film; only the grid update kernels
+// (one or two items per thread) pack.
+
+// Packed operands of R rows (wrap signs folded into ym, yp).
+struct Packed {
+  uint32_t S, xm, xp, ym, yp, z0, Zs;
+  uint32_t kx, ky0;
+};
+
+// Row mask of the low B bits of each byte.
+template <uint32_t R>
+__device__ __forceinline__ constexpr uint32_t slot_mask() {
+  return 0x01010101u * ((1u << (8 / R)) - 1u);
+}
+
+template <uint32_t R>
+__device__ __forceinline__ void fetch_packed(const FilmCtx& c, uint32_t kx, uint32_t ky0, Packed& p) {
+  constexpr uint32_t B = 8 / R;
+  p.kx = kx;
+  p.ky0 = ky0;
+  p.S = p.xm = p.xp = p.ym = p.yp = p.z0 = p.Zs = 0;
+  const uint32_t valid = c.last_mask;  // the row's sites, all in the low B bits of each byte
+  const uint32_t negm = (c.y_mode != kYPbc) ? valid : 0u;
+#pragma unroll
+  for (uint32_t j = 0; j < R; j++) {
+    const uint32_t ky = ky0 + j;
+    Fetched f;
+    fetch_word(c, kx, ky, 0, f);
+    const uint32_t X = (kx + ky + 1 + c.colour) & 1u;
+    const uint32_t zs = z_shifted<false>(c, f, X, true) & valid;
+    const uint32_t sh = j * B;
+    p.S |= f.S << sh;
+    p.xm |= f.xm << sh;
+    p.xp |= f.xp << sh;
+    p.ym |= (f.ym ^ (ky > 1 ? 0u : negm)) << sh;
+    p.yp |= (f.yp ^ (ky < c.Ly ? 0u : negm)) << sh;
+    p.z0 |= f.z0 << sh;
+    p.Zs |= zs << sh;
+  }
+}
+
+// The word of each of the R rows back into its own array.
+template <uint32_t R>
+__device__ __forceinline__ void store_packed(const FilmCtx& c, const Packed& p, uint32_t v) {
+  constexpr uint32_t B = 8 / R;
+#pragma unroll
+  for (uint32_t j = 0; j < R; j++) {
+    const uint32_t ky = p.ky0 + j;
+    const uint32_t row = (p.kx - 1) * c.Ly + (ky - 1);
+    const uint32_t X = (p.kx + ky + 1 + c.colour) & 1u;
+    uint32_t* __restrict__ P = X ? c.plane1 : c.plane0;
+    ISG_ST(P, row * c.Wp, c.plane_words, 17, (v >> (j * B)) & slot_mask<R>());
+  }
+}
+
+// Metropolis decisions of the packed word: the flip mask (packed).  MEAS:
+// parks the counts and the packed other-array word like decide_word.
+template <uint32_t R, bool FAST, bool MEAS>
+__device__ __forceinline__ uint32_t decide_packed(const FilmCtx& c, const Packed& p,
+                                                  const uint32_t* __restrict__ s_thr,
+                                                  const uint32_t* __restrict__ s_alw, uint32_t* stash) {
+  constexpr uint32_t B = 8 / R;
+  const uint32_t Lx = c.Lx, kx = p.kx;
+  const uint32_t S = p.S;
+  const uint32_t xm_on = (kx > 1 || c.x_pbc) ? 0xFFFFFFFFu : 0u;
+  const uint32_t xp_on = (kx < Lx || c.x_pbc) ? 0xFFFFFFFFu : 0u;
+  const uint32_t a0 = ~(S ^ p.xm) & xm_on;
+  const uint32_t a1 = ~(S ^ p.xp) & xp_on;
+  const uint32_t a2 = ~(S ^ p.ym);
+  const uint32_t a3 = ~(S ^ p.yp);
+  const uint32_t a4 = ~(S ^ p.z0);
+  const uint32_t a5 = ~(S ^ p.Zs);
+  const uint32_t s1 = a0 ^ a1 ^ a2, k1 = maj3(a0, a1, a2);
+  const uint32_t s2 = a3 ^ a4 ^ a5, k2 = maj3(a3, a4, a5);
+  const uint32_t c0 = s1 ^ s2, k3 = s1 & s2;
+  const uint32_t c1 = k1 ^ k2 ^ k3, c2 = maj3(k1, k2, k3);
+  if (MEAS) stash_counts(stash, c0, c1, c2, p.z0);
+
+  const uint32_t cls = row_class(kx, Lx);
+  uint32_t alw = 0;
+  if (!FAST) {
+    const uint4* m4 = reinterpret_cast<const uint4*>(s_alw + cls * 16);
+    const uint4 ma = m4[0], mb = m4[1], mc = m4[2], md = m4[3];
+    const uint32_t v0 = (S & ma.y) | (~S & ma.x);
+    const uint32_t v1 = (S & ma.w) | (~S & ma.z);
+    const uint32_t v2 = (S & mb.y) | (~S & mb.x);
+    const uint32_t v3 = (S & mb.w) | (~S & mb.z);
+    const uint32_t v4 = (S & mc.y) | (~S & mc.x);
+    const uint32_t v5 = (S & mc.w) | (~S & mc.z);
+    const uint32_t v6 = (S & md.y) | (~S & md.x);
+    const uint32_t v7 = (S & md.w) | (~S & md.z);
+    const uint32_t w0 = (c0 & v1) | (~c0 & v0);
+    const uint32_t w1 = (c0 & v3) | (~c0 & v2);
+    const uint32_t w2 = (c0 & v5) | (~c0 & v4);
+    const uint32_t w3 = (c0 & v7) | (~c0 & v6);
+    const uint32_t x0 = (c1 & w1) | (~c1 & w0);
+    const uint32_t x1 = (c1 & w3) | (~c1 & w2);
+    alw = (c2 & x1) | (~c2 & x0);
+  }
+  const uint32_t T0 = (S & 0x55555555u) | ((c0 & 0x55555555u) << 1);
+  const uint32_t T1 = ((S >> 1) & 0x55555555u) | (c0 & 0xAAAAAAAAu);
+  const uint32_t T2 = (c1 & 0x55555555u) | ((c2 & 0x55555555u) << 1);
+  const uint32_t T3 = ((c1 >> 1) & 0x55555555u) | (c2 & 0xAAAAAAAAu);
+  uint32_t U[4];
+  U[0] = (T0 & 0x33333333u) | ((T2 & 0x33333333u) << 2);
+  U[1] = (T1 & 0x33333333u) | ((T3 & 0x33333333u) << 2);
+  U[2] = ((T0 >> 2) & 0x33333333u) | (T2 & 0xCCCCCCCCu);
+  U[3] = ((T1 >> 2) & 0x33333333u) | (T3 & 0xCCCCCCCCu);
+
+  const uint32_t clsb = (cls * 64u) * 0x01010101u;
+  const char* tb = reinterpret_cast<const char*>(s_thr);
+  const uint32_t ncalls = c.last_calls;  // calls of one row (q < ncalls)
+  const uint32_t rowb = (kx - 1) * c.Ly + (p.ky0 - 1);
+  uint32_t lt = 0;
+  // call Q (0..7) of the packed word: row Q / B's call Q % B, whose sites sit
+  // at bits Q + 8 I; their table indices are nibbles of U[Q & 3] (the low or
+  // high nibble of each byte for Q < 4 or Q >= 4)
+  auto call = [&](auto qc) {
+    constexpr uint32_t Q = decltype(qc)::value;
+    constexpr uint32_t j = Q / B, q = Q % B;
+    if (q < ncalls) {
+      const uint32_t X = (kx + p.ky0 + j + 1 + c.colour) & 1u;
+      uint32_t u[4];
+      PhiloxRow(rowb + j, c.sweep, X, c.rk0, c.rk1).draw(q, u);
+      const uint32_t Uq = U[Q & 3];
+      const uint32_t Y = (Q < 4 ? ((Uq << 2) & 0x3C3C3C3Cu) : ((Uq >> 2) & 0x3C3C3C3Cu)) | clsb;
+      site_one<FAST, Q, 0>(lt, tb, Y, u[0]);
+      site_one<FAST, Q, 1>(lt, tb, Y, u[1]);
+      site_one<FAST, Q, 2>(lt, tb, Y, u[2]);
+      site_one<FAST, Q, 3>(lt, tb, Y, u[3]);
+    }
+  };
+  call(std::integral_constant<uint32_t, 0>{});
+  call(std::integral_constant<uint32_t, 4>{});
+  call(std::integral_constant<uint32_t, 1>{});
+  call(std::integral_constant<uint32_t, 5>{});
+  call(std::integral_constant<uint32_t, 2>{});
+  call(std::integral_constant<uint32_t, 6>{});
+  call(std::integral_constant<uint32_t, 3>{});
+  call(std::integral_constant<uint32_t, 7>{});
+  uint32_t valid = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < R; j++) valid |= c.last_mask << (j * B);
+  return (lt | alw) & valid;
+}
+
+// Record sums of a packed word (all its rows lie in layer kx): as word_sums,
+// over the valid sites of every row.
+template <uint32_t R>
+__device__ __forceinline__ LayerSums packed_sums(const FilmCtx& c, uint32_t kx, uint32_t fl, uint32_t v,
+                                                 const uint32_t* stash) {
+  constexpr uint32_t B = 8 / R;
+  uint32_t valid = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < R; j++) valid |= c.last_mask << (j * B);
+  const int nv = __popc(valid);
+  const uint32_t c0 = stash[0], c1 = stash[1], c2 = stash[2], z0 = stash[3];
+  const int D = 4 + ((kx > 1 || c.x_pbc) ? 1 : 0) + ((kx < c.Lx || c.x_pbc) ? 1 : 0);
+  const int n_old = __popc(c0 & valid) + 2 * __popc(c1 & valid) + 4 * __popc(c2 & valid);
+  const int n_fl = __popc(c0 & fl) + 2 * __popc(c1 & fl) + 4 * __popc(c2 & fl);
+  LayerSums r;
+  r.layer = kx - 1;
+  r.b = 2 * (n_old + D * __popc(fl) - 2 * n_fl) - D * nv;
+  r.m = 2 * (__popc(v & valid) + __popc(z0 & valid)) - 2 * nv;
+  return r;
+}
+
+// The R rows of a group, and, for the group holding ky = 1, then the group
+// holding ky = Ly of the wrap partner layer (fetched after the first group is
+// stored, as update_fetched does with single rows).  MEAS: the record sums of
+// both groups (the seam correction taken on the rows ky = 1 and ky = Ly).
+template <uint32_t R, bool FAST, bool MEAS, typename AccOf>
+__device__ __forceinline__ void update_packed(const FilmCtx& c, const Packed& p, const uint32_t* s_thr,
+                                              const uint32_t* s_alw, uint32_t* stash, LayerSums* r1,
+                                              LayerSums* r2, AccOf acc_of) {
+  constexpr uint32_t B = 8 / R;
+  const uint32_t fl = decide_packed<R, FAST, MEAS>(c, p, s_thr, s_alw, stash);
+  const uint32_t v = p.S ^ fl;
+  store_packed<R>(c, p, v);
+  if (MEAS) *r1 = packed_sums<R>(c, p.kx, fl, v, stash);
+  if (p.ky0 != 1) return;
+  if (MEAS) {  // a pair lane adds its first group's sums now (its own atomics), not across the partner's draws
+    add_lane_sums(acc_of(), *r1);
+    r1->layer = 0xFFFFFFFFu;
+  }
+  const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - p.kx) : p.kx;
+  Packed g;
+  fetch_packed<R>(c, kx2, c.Ly - R + 1, g);
+  if (MEAS) {
+    // rows ky = 1 (slot 0 of this group) and ky = Ly (slot R - 1 of g)
+    Fetched gl;
+    gl.S = (g.S >> ((R - 1) * B)) & slot_mask<R>();
+    gl.z0 = (g.z0 >> ((R - 1) * B)) & slot_mask<R>();
+    stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, 0, v & slot_mask<R>(), stash[3] & slot_mask<R>(), gl) : 0u;
+  }
+  const uint32_t fl2 = decide_packed<R, FAST, MEAS>(c, g, s_thr, s_alw, stash);
+  const uint32_t v2 = g.S ^ fl2;
+  store_packed<R>(c, g, v2);
+  if (MEAS) {
+    *r2 = packed_sums<R>(c, kx2, fl2, v2, stash);
+    r2->b += (int)stash[4];
+  }
+}
+
+// Group of packed update item `item`: the first Lx items are the groups
+// holding ky = 1 (whose threads then update the wrap partner's last group),
+// the others the middle groups of each layer.  (dm, dl) divide by
+// Ly / R - 2 (by 1 when that is 0).
+template <uint32_t R>
+__device__ __forceinline__ void item_group(const FilmCtx& c, uint32_t item, uint32_t dm, uint32_t dl, uint32_t& kx,
+                                           uint32_t& ky0) {
+  const bool pair = item < c.Lx;
+  const uint32_t r = pair ? 0u : item - c.Lx;
+  const uint32_t q = fastdiv(r, dm, dl);
+  kx = (pair ? item : q) + 1;
+  ky0 = pair ? 1u : (r - q * (c.Ly / R - 2) + 1) * R + 1;
+}
+
+// The packed items of one block (as sweep_block's word items), one after
+// another: a packed group already holds R rows' loads in flight.
+template <uint32_t R, bool FAST, uint32_t ITEMS, bool MEAS, typename AccOf>
+__device__ __forceinline__ void sweep_block_packed(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dm,
+                                                   uint32_t dl, const uint32_t* __restrict__ s_thr,
+                                                   const uint32_t* __restrict__ s_alw, bool meas, AccOf acc_of,
+                                                   uint32_t* stash) {
+#pragma unroll 1
+  for (uint32_t it = 0; it < ITEMS; it++) {
+    const uint32_t item = first + threadIdx.x + it * kFilmThreads;
+    const bool mine = item < items;
+    Packed p;
+    if (mine) {
+      uint32_t kx, ky0;
+      item_group<R>(c, item, dm, dl, kx, ky0);
+      fetch_packed<R>(c, kx, ky0, p);
+    }
+    LayerSums r1, r2;
+    if (MEAS && meas) {
+      if (mine) update_packed<R, FAST, true>(c, p, s_thr, s_alw, stash, &r1, &r2, acc_of);
+      add_layer_sums(acc_of(), r1);
+      add_lane_sums(acc_of(), r2);
+    } else if (mine) {
+      update_packed<R, FAST, false>(c, p, s_thr, s_alw, stash, &r1, &r2, acc_of);
+    }
+  }
+}
+
+// The packed items of one block, each group's rows decided one at a time
+// with the single-row body (update_fetched): rows ky0 .. ky0+R-1 of layer
+// kx, and for the group holding ky = 1 (whose row 1 then updates its wrap
+// partner, row Ly of layer kx') the other rows of the partner's group.  The
+// record sums of a group's rows (one layer) and of the partner's rows
+// (another) are added up in registers and then added like a single word's.
+template <bool FAST, bool MEAS, bool PATHS4, typename AccOf>
+__device__ __forceinline__ void sweep_block_rows(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dm,
+                                                 uint32_t dl, const uint32_t* __restrict__ s_thr,
+                                                 const uint32_t* __restrict__ s_alw, bool meas, AccOf acc_of,
+                                                 uint32_t* stash) {
+  const uint32_t R = c.pack;
+  const uint32_t item = first + threadIdx.x;
+  const bool mine = item < items;
+  LayerSums g1, g2;
+  if (mine) {
+    uint32_t kx, ky0;
+    const uint32_t G2 = c.Ly / R - 2;
+    const bool pair = item < c.Lx;
+    const uint32_t r = pair ? 0u : item - c.Lx;
+    const uint32_t q = fastdiv(r, dm, dl);
+    kx = (pair ? item : q) + 1;
+    ky0 = pair ? 1u : (r - q * G2 + 1) * R + 1;
+    const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - kx) : kx;
+    if (MEAS) {
+      g1.layer = kx - 1;
+      if (pair) g2.layer = kx2 - 1;
+    }
+    const uint32_t nrows = pair ? 2 * R - 1 : R;  // the partner row itself comes with row 1
+#pragma unroll 1
+    for (uint32_t i = 0; i < nrows; i++) {
+      const bool own = i < R;
+      const uint32_t rkx = own ? kx : kx2, rky = own ? ky0 + i : c.Ly - R + 1 + (i - R);
+      Fetched f;
+      fetch_word(c, rkx, rky, 0, f);
+      if (MEAS && meas) {
+        LayerSums a, b;
+        update_fetched<FAST, true, PATHS4>(c, f, s_thr, s_alw, stash, &a, &b);
+        LayerSums& g = own ? g1 : g2;
+        g.m += a.m;
+        g.b += a.b;
+        if (b.layer != 0xFFFFFFFFu) {  // the partner row of row 1
+          g2.m += b.m;
+          g2.b += b.b;
+        }
+      } else {
+        update_fetched<FAST, false, PATHS4>(c, f, s_thr, s_alw);
+      }
+    }
+  }
+  if (MEAS && meas) {
+    add_layer_sums(acc_of(), g1);
+    add_lane_sums(acc_of(), g2);
+  }
+}
+
 }  // namespace
 
 // The words of one block of words_per_block(ITEMS) consecutive words: each
@@ -635,7 +951,7 @@ __device__ __forceinline__ void update_fetched_quarter(const FilmCtx& c, const F
 // sums go into the film's per-layer accumulators acc_of() (a pointer made
 // where it is used, not kept across the draws); s_stash holds kStashSlots
 // words per thread.
-template <bool FAST, uint32_t ITEMS, bool MEAS, bool PATHS4, bool H3, typename AccOf>
+template <bool FAST, uint32_t ITEMS, bool MEAS, bool PATHS4, bool H3, bool PK, typename AccOf>
 __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dwm,
                                             uint32_t dwl, uint32_t dym, uint32_t dyl,
                                             const uint32_t* __restrict__ s_thr, const uint32_t* __restrict__ s_alw,
@@ -662,6 +978,18 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
     return;
   }
   constexpr uint32_t NI = ITEMS == 0 ? 1 : ITEMS;
+  if (PK && ITEMS == 1 && c.pack > 1) {  // the same for the whole film (the block)
+    // fast-table plain launches decide a group's rows at once; the summing
+    // and exact-table launches, whose registers have no room for the packed
+    // body, take the group's rows one after another
+    if (FAST && !MEAS) {
+      if (c.pack == 4) sweep_block_packed<4, FAST, 1, MEAS>(c, first, items, dym, dyl, s_thr, s_alw, meas, acc_of, stash);
+      else sweep_block_packed<2, FAST, 1, MEAS>(c, first, items, dym, dyl, s_thr, s_alw, meas, acc_of, stash);
+    } else {
+      sweep_block_rows<FAST, MEAS, PATHS4>(c, first, items, dym, dyl, s_thr, s_alw, meas, acc_of, stash);
+    }
+    return;
+  }
   Fetched fw[NI];
   bool mine[NI];
 #pragma unroll
@@ -705,8 +1033,11 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // its update, so the write overlaps the launch's other blocks.
 enum : uint32_t { kUpdPlain = 0, kUpdAccumulate = 1, kUpdWriteRecord = 2 };
 
-template <bool FAST, uint32_t ITEMS, uint32_t MODE>
-__global__ void __launch_bounds__(kFilmThreads, (ITEMS == 1 && MODE != kUpdAccumulate) ? kMultiMinBlocks1
+template <bool FAST, uint32_t ITEMS, uint32_t MODE, bool PK = false>
+__global__ void __launch_bounds__(kFilmThreads, PK ? (MODE == kUpdAccumulate ? (FAST ? kMultiMinBlocks - 1
+                                                                                    : kMultiMinBlocks - 2)
+                                                                           : kMultiMinBlocks)
+                                                : (ITEMS == 1 && MODE != kUpdAccumulate) ? kMultiMinBlocks1
                                                 : (FAST || (ITEMS < 2 && MODE != kUpdAccumulate))
                                                     ? kMultiMinBlocks : kMultiMinBlocks - 1)
 update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ owner,
@@ -764,8 +1095,12 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     const uint32_t first = (vb - s_d.upd_block_begin) * words_per_block(ITEMS);
     // two words per thread, and the exact table: the register budget keeps
     // the two-path decision
-    sweep_block<FAST, ITEMS, MEAS, FAST && ITEMS != 2, false>(c, first, s_d.upd_items, s_d.divw_m, s_d.divw_l, s_d.divy_m, s_d.divy_l, s_lo,
-                                   s_alw, meas, acc_of, s_stash);
+    // packed thin films: group items and their divisor
+    c.pack = PK ? s_d.pack : 1u;
+    const bool pk = c.pack > 1;
+    sweep_block<FAST, ITEMS, MEAS, FAST && ITEMS != 2, false, PK>(
+        c, first, pk ? s_d.pk_items : s_d.upd_items, s_d.divw_m, s_d.divw_l, pk ? s_d.pk_divm : s_d.divy_m,
+        pk ? s_d.pk_divl : s_d.divy_l, s_lo, s_alw, meas, acc_of, s_stash);
   }
 }
 
@@ -774,8 +1109,8 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
 // from the constant bank; block b updates words b * words_per_block(ITEMS)
 // onwards.  MEAS: half-sweep 1 before a record, whose sums go into the
 // film's accumulators acc.
-template <bool FAST, uint32_t ITEMS, bool MEAS>
-__global__ void __launch_bounds__(kFilmThreads, kFilmMinBlocks)
+template <bool FAST, uint32_t ITEMS, bool MEAS, bool PK = false>
+__global__ void __launch_bounds__(kFilmThreads, PK && MEAS ? kFilmMinBlocks - 1 : kFilmMinBlocks)
 update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ pool, uint32_t colour,
                    uint32_t sweep, int64_t* __restrict__ acc) {
   pdl_trigger();
@@ -801,8 +1136,11 @@ update_film_kernel(const __grid_constant__ FilmDesc d, uint32_t* __restrict__ po
   auto acc_of = [acc]() { return reinterpret_cast<unsigned long long*>(acc); };
   // the Philox head with round 3's product hoisted (PhiloxRow3) wherever the
   // registers allow it: not in the recording launch
-  sweep_block<FAST, ITEMS, MEAS, true, !MEAS>(c, blockIdx.x * words_per_block(ITEMS), d.upd_items, d.divw_m, d.divw_l, d.divy_m,
-                                 d.divy_l, s_thr, s_alw, MEAS, acc_of, s_stash);
+  c.pack = PK ? d.pack : 1u;
+  const bool pk = c.pack > 1;
+  sweep_block<FAST, ITEMS, MEAS, true, !MEAS, PK>(c, blockIdx.x * words_per_block(ITEMS), pk ? d.pk_items : d.upd_items,
+                                              d.divw_m, d.divw_l, pk ? d.pk_divm : d.divy_m,
+                                              pk ? d.pk_divl : d.divy_l, s_thr, s_alw, MEAS, acc_of, s_stash);
 }
 
 // ------------------------------------------------------------ measurement
@@ -1020,6 +1358,7 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
   c.plane0 = s_planes;
   c.plane1 = s_planes + words;
   c.seam_same = seam_joins_one_colour(Lx, Ly, s_d.y_mode);
+  c.pack = 1;  // the resident kernel updates single rows
   const uint32_t items = s_d.upd_items;
   const uint32_t m_every = s_d.measure_every;
   uint32_t rec_next = s_d.rec_next;
@@ -1185,8 +1524,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, 
 
 namespace {
 
+// pk: one item per thread and some film of the launch packs rows
 template <uint32_t MODE>
-auto update_variant(bool exact, uint32_t items) {
+auto update_variant(bool exact, uint32_t items, bool pk) {
+  if (pk) return exact ? update_kernel<false, 1, MODE, true> : update_kernel<true, 1, MODE, true>;
   return exact ? (items == 2 ? update_kernel<false, 2, MODE>
                              : items == 1 ? update_kernel<false, 1, MODE> : update_kernel<false, 0, MODE>)
                : (items == 2 ? update_kernel<true, 2, MODE>
@@ -1194,7 +1535,8 @@ auto update_variant(bool exact, uint32_t items) {
 }
 
 template <bool MEAS>
-auto update_film_variant(bool exact, uint32_t items) {
+auto update_film_variant(bool exact, uint32_t items, bool pk) {
+  if (pk) return exact ? update_film_kernel<false, 1, MEAS, true> : update_film_kernel<true, 1, MEAS, true>;
   return exact ? (items == 2 ? update_film_kernel<false, 2, MEAS>
                              : items == 1 ? update_film_kernel<false, 1, MEAS> : update_film_kernel<false, 0, MEAS>)
                : (items == 2 ? update_film_kernel<true, 2, MEAS>
@@ -1204,12 +1546,13 @@ auto update_film_variant(bool exact, uint32_t items) {
 }  // namespace
 
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          uint32_t items, int64_t* part, int64_t* records, bool accumulate, uint32_t rec_done,
-                          cudaStream_t st) {
+                          uint32_t items, bool pack, int64_t* part, int64_t* records, bool accumulate,
+                          uint32_t rec_done, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  auto* kern = (accumulate && colour == 1) ? update_variant<kUpdAccumulate>(exact, items)
-               : (rec_done && colour == 0) ? update_variant<kUpdWriteRecord>(exact, items)
-                                           : update_variant<kUpdPlain>(exact, items);
+  const bool pk = pack && items == 1;
+  auto* kern = (accumulate && colour == 1) ? update_variant<kUpdAccumulate>(exact, items, pk)
+               : (rec_done && colour == 0) ? update_variant<kUpdWriteRecord>(exact, items, pk)
+                                           : update_variant<kUpdPlain>(exact, items, pk);
   return launch_pdl(kern, grid, kFilmThreads, 0, st, (const FilmDesc*)L.films, (const uint32_t*)L.owner_upd,
                     (const LaunchHdr*)L.hdr, pool, colour, k, part, records, rec_done);
 }
@@ -1217,10 +1560,11 @@ cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uin
 cudaError_t launch_update_film(const FilmDesc& d, uint32_t* pool, uint32_t colour, uint32_t sweep, uint32_t items,
                                int64_t* acc, cudaStream_t st) {
   const uint32_t ipb = words_per_block(items);
-  const uint32_t grid = (d.upd_items + ipb - 1) / ipb;
+  const uint32_t grid = (grid_items(d, items) + ipb - 1) / ipb;
   if (grid == 0) return cudaSuccess;
   const bool exact = d.has_never != 0;
-  auto* kern = acc ? update_film_variant<true>(exact, items) : update_film_variant<false>(exact, items);
+  const bool pk = items == 1 && d.pack > 1;
+  auto* kern = acc ? update_film_variant<true>(exact, items, pk) : update_film_variant<false>(exact, items, pk);
   return launch_pdl(kern, grid, kFilmThreads, 0, st, d, pool, colour, sweep, acc);
 }
 

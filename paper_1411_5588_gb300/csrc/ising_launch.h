@@ -37,6 +37,16 @@ __host__ __device__ inline uint64_t acc_offset(const FilmDesc& d) {
   return d.part_off + 2ull * d.Lx * d.meas_bpl;
 }
 
+// Films of at least this many rows pack two rows per word when they qualify
+// (fill_geometry); four rows pack at any size.
+constexpr uint32_t kPack2Rows = 8192;
+
+// Items of a film in the grid update kernels with `items` words per thread:
+// thin films pack rows at one item per thread only.
+__host__ __device__ inline uint32_t grid_items(const FilmDesc& d, uint32_t items) {
+  return (items == 1 && d.pack > 1) ? d.pk_items : d.upd_items;
+}
+
 // Measurement blocks of one film.
 inline uint32_t meas_units(const FilmDesc& d) {
   return d.meas_lpu > 1 ? (d.Lx + d.meas_lpu - 1) / d.meas_lpu : d.Lx * d.meas_bpl;
@@ -69,9 +79,11 @@ struct LaunchSet {
 // part; with rec_done > 0 (colour 0) the films that recorded after rec_done
 // sweeps have that record written into their rings in records by this
 // launch (the chunk's last record goes through launch_record instead).
+// pack: some film of the launch packs rows (FilmDesc::pack > 1; with items
+// 1 its owner table counts groups of rows, grid_items).
 cudaError_t launch_update(const LaunchSet& L, uint32_t grid, uint32_t* pool, uint32_t colour, uint32_t k, bool exact,
-                          uint32_t items, int64_t* part, int64_t* records, bool accumulate, uint32_t rec_done,
-                          cudaStream_t st);
+                          uint32_t items, bool pack, int64_t* part, int64_t* records, bool accumulate,
+                          uint32_t rec_done, cudaStream_t st);
 // One half-sweep of a single film whose descriptor (with `sweep` absolute) is
 // passed by value; acc (colour 1 of a recorded sweep, else null): the film's
 // accumulators.

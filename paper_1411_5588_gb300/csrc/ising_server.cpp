@@ -342,7 +342,7 @@ void ising_server::loop() {
       uint32_t* om = ou + cap_upd;
       for (size_t f = 0; f < F.h.size(); f++) {
         const FilmDesc& d = F.h[f];
-        const uint32_t nb = (d.upd_items + words_per_block(F.items) - 1) / words_per_block(F.items);
+        const uint32_t nb = (grid_items(d, F.items) + words_per_block(F.items) - 1) / words_per_block(F.items);
         for (uint32_t b = 0; b < nb; b++) ou[d.upd_block_begin + b] = (uint32_t)f;
         for (uint32_t b = 0; b < meas_units(d); b++) om[d.meas_block_begin + b] = (uint32_t)f;
       }

@@ -5,8 +5,9 @@ Philox stream, same four-phase schedule, same binary64 thresholds -- so the
 spin configuration and every record must be identical after any number of
 sweeps.  Shapes cover several words per row with a ragged last word, a
 single partial word, Lz = 2 (double z bonds), Ly = 2, Lx = 1, odd and even
-Lx + Ly (the Eq. 11 wrap joining equal or opposite colours), periodic x, and
-the degenerate temperatures beta = 0 and T -> 0.
+Lx + Ly (the Eq. 11 wrap joining equal or opposite colours), periodic x,
+thin films whose rows the one-word grid kernels pack two or four to a
+register, and the degenerate temperatures beta = 0 and T -> 0.
 """
 import math
 
@@ -35,6 +36,13 @@ CASES = [
     (3, 3, 6, ig.Y_GAPBC, ig.X_FREE, 1.0, 0.0, 1.5, ig.INIT_ALL_UP, 0.0),
     (2, 9, 34, ig.Y_APBC, ig.X_PBC, 0.25, -0.2, 2.8, ig.INIT_RANDOM, 0.0),
     (16, 12, 96, ig.Y_GAPBC, ig.X_FREE, 0.55, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01),
+    # thin films, several rows per packed word in the one-word grid kernels
+    (6, 12, 16, ig.Y_APBC, ig.X_FREE, 0.35, 0.0, 2.6, ig.INIT_RANDOM, 0.0),
+    (5, 10, 30, ig.Y_GAPBC, ig.X_FREE, 0.45, 0.0, 3.0, ig.INIT_SLAB_Y, 0.02),
+    (7, 16, 12, ig.Y_GAPBC, ig.X_FREE, -0.5, 0.0, 2.3, ig.INIT_SLAB_Y, 0.01),
+    (4, 6, 20, ig.Y_PBC, ig.X_PBC, 0.0, 0.15, 3.4, ig.INIT_RANDOM, 0.0),
+    (9, 8, 4, ig.Y_GAPBC, ig.X_FREE, 0.6, 0.0, 2.9, ig.INIT_RANDOM, 0.0),
+    (6, 8, 16, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 1e-3, ig.INIT_RANDOM, 0.0),
 ]
 
 
@@ -69,6 +77,43 @@ def test_sweeps_bit_exact(case, shape):
         assert np.array_equal(g.get_spins(), o.get_spins()), f"spins differ after {done} sweeps"
     assert np.array_equal(g.measure(), o.measure())
     g.close()
+
+
+THIN = [  # films of at least 8192 rows that pack two rows per word (Lz 12, 30), and one that packs four
+    (48, 172, 30, ig.Y_GAPBC, ig.X_FREE, 0.45, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01),
+    (64, 130, 12, ig.Y_APBC, ig.X_PBC, 0.0, 0.1, 2.7, ig.INIT_RANDOM, 0.0),
+    (33, 256, 14, ig.Y_GAPBC, ig.X_FREE, -0.4, 0.0, 2.4, ig.INIT_RANDOM, 0.0),
+    (40, 208, 16, ig.Y_PBC, ig.X_FREE, 0.3, 0.0, 3.2, ig.INIT_SLAB_Y, 0.02),
+]
+
+
+@pytest.mark.parametrize("case", THIN, ids=[f"{c[0]}x{c[1]}x{c[2]}-y{c[3]}" for c in THIN])
+def test_large_thin_films_bit_exact(case):
+    """Thin films large enough to pack two rows per word at one word per
+    thread (and Lz = 16, four): the single-film kernel, then the same film in
+    a batch beside a film that does not pack, with records every 1-3 sweeps
+    (the summing launches take the rows one at a time)."""
+    g, o = _pair(case, shape=ig.SHAPE_GRID_1)
+    for n, m in ((1, 1), (6, 2), (21, 3)):
+        g.sweep(n, m)
+        assert np.array_equal(g.read_series(), o.sweep(n, m)), n
+        assert np.array_equal(g.get_spins(), o.get_spins()), n
+    g.close()
+    Lx, Ly, Lz, ym, xm, H1, H, T, kind, flip = case
+    specs = [dict(Lx=Lx, Ly=Ly, Lz=Lz, y_mode=ym, x_mode=xm, H1=H1, H=H, T=T, seed=7, replica=1, init_kind=kind,
+                  flip_p=flip, measure_every=2),
+             dict(Lx=6, Ly=9, Lz=70, T=2.5, H1=0.2, seed=7, replica=2, init_kind=ig.INIT_RANDOM, measure_every=1)]
+    b = ig.Batch(specs, lanes=1)
+    b.set_shape(ig.SHAPE_GRID_1)
+    b.sweep(3, False)
+    b.sweep(33, True)
+    for i, sp in enumerate(specs):
+        o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], y_mode=sp.get("y_mode", 0),
+                   x_mode=sp.get("x_mode", 0), H=sp.get("H", 0.0), replica=sp["replica"])
+        o.init(sp["init_kind"], sp.get("flip_p", 0.0))
+        assert np.array_equal(b.read_series(i), o.sweep(36, sp["measure_every"])), i
+        assert np.array_equal(b.get_spins(i), o.get_spins()), i
+    b.close()
 
 
 def test_measure_matches_oracle_on_given_spins():
