@@ -46,7 +46,7 @@ int check_film(int Lx, int Ly, int Lz, double T, int y_mode, int x_mode) {
   if (y_mode < ISING_Y_GAPBC || y_mode > ISING_Y_APBC) return fail(ISING_EINVAL, "bad y_mode %d", y_mode);
   if (x_mode != ISING_X_FREE && x_mode != ISING_X_PBC) return fail(ISING_EINVAL, "bad x_mode %d", x_mode);
   if (x_mode == ISING_X_PBC && (Lx < 2 || (Lx & 1))) return fail(ISING_EINVAL, "periodic x needs even Lx >= 2");
-  const double plane = (double)Lx * (double)Ly * (((Lz / 2 + 31) / 32 + 3) / 4 * 4);
+  const double plane = (double)Lx * (double)Ly * ((Lz / 2 + 31) / 32);
   if (plane >= 2147483648.0) return fail(ISING_EINVAL, "film too large (2^31 words per parity plane at most)");
   return ISING_OK;
 }
@@ -57,8 +57,8 @@ void fill_geometry(FilmDesc& d, int Lx, int Ly, int Lz, int y_mode, int x_mode, 
   d.Lz = (uint32_t)Lz;
   d.n = (uint32_t)Lz / 2;
   d.W = (d.n + 31) / 32;
-  d.Wp = (d.W + 3) / 4 * 4;
-  d.nq = d.Wp / 4;
+  d.Wp = d.W;  // rows contiguous: no padding words
+  d.nq = (d.Wp + 3) / 4;
   const uint32_t r = d.n - 32 * (d.W - 1);  // valid sites of the last word, 1..32
   uint32_t mask = 0;
   for (uint32_t l = 0; l < r; l++) mask |= 1u << bitpos(l);

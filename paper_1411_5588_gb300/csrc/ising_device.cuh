@@ -4,8 +4,7 @@
 // (kx-1)*Ly + (ky-1).  Each row is split by the parity X = z0 & 1 of
 // z0 = kz-1 into two arrays of n = Lz/2 sites, site j of array X being
 // z0 = 2j + X.  An array is W = ceil(n/32) 32-bit words, stored with a row
-// stride of Wp = W rounded up to a multiple of 4 words (16 bytes, so a thread
-// moves four words with one 128-bit access; the extra words stay 0).  The
+// stride of Wp = W words (no padding: every kernel moves single words).  The
 // film's words are laid out [X][row][w] (one "plane" per parity, rows
 // contiguous, z fastest).
 // Inside a word, local site l (0..31) sits at bit (l >> 2) + 8*(l & 3), so the
@@ -33,7 +32,7 @@ enum : uint32_t { kYGapbc = 0, kYPbc = 1, kYApbc = 2 };
 // `rec_next` are advanced by kernels so that captured graphs can be replayed.
 struct FilmDesc {
   uint32_t Lx, Ly, Lz, n, W;   // n = Lz/2 sites per array, W words per array
-  uint32_t Wp, nq;             // row stride in words (multiple of 4), nq = Wp / 4
+  uint32_t Wp, nq;             // row stride in words (= W), nq = ceil(Wp / 4)
   uint32_t y_mode, x_pbc;
   uint32_t key0, key1;         // Philox key
   uint32_t last_mask;          // valid bits of word W-1
