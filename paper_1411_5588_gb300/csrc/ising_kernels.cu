@@ -695,12 +695,11 @@ __device__ __forceinline__ void store_packed(const FilmCtx& c, const Packed& p, 
   }
 }
 
-// Metropolis decisions of the packed word: the flip mask (packed).  MEAS:
-// parks the counts and the packed other-array word like decide_word.
-template <uint32_t R, bool FAST, bool MEAS>
+// Metropolis decisions of the packed word: the flip mask (packed).
+template <uint32_t R, bool FAST>
 __device__ __forceinline__ uint32_t decide_packed(const FilmCtx& c, const Packed& p,
                                                   const uint32_t* __restrict__ s_thr,
-                                                  const uint32_t* __restrict__ s_alw, uint32_t* stash) {
+                                                  const uint32_t* __restrict__ s_alw) {
   constexpr uint32_t B = 8 / R;
   const uint32_t Lx = c.Lx, kx = p.kx;
   const uint32_t S = p.S;
@@ -716,7 +715,6 @@ __device__ __forceinline__ uint32_t decide_packed(const FilmCtx& c, const Packed
   const uint32_t s2 = a3 ^ a4 ^ a5, k2 = maj3(a3, a4, a5);
   const uint32_t c0 = s1 ^ s2, k3 = s1 & s2;
   const uint32_t c1 = k1 ^ k2 ^ k3, c2 = maj3(k1, k2, k3);
-  if (MEAS) stash_counts(stash, c0, c1, c2, p.z0);
 
   const uint32_t cls = row_class(kx, Lx);
   uint32_t alw = 0;
@@ -786,62 +784,21 @@ __device__ __forceinline__ uint32_t decide_packed(const FilmCtx& c, const Packed
   return (lt | alw) & valid;
 }
 
-// Record sums of a packed word (all its rows lie in layer kx): as word_sums,
-// over the valid sites of every row.
-template <uint32_t R>
-__device__ __forceinline__ LayerSums packed_sums(const FilmCtx& c, uint32_t kx, uint32_t fl, uint32_t v,
-                                                 const uint32_t* stash) {
-  constexpr uint32_t B = 8 / R;
-  uint32_t valid = 0;
-#pragma unroll
-  for (uint32_t j = 0; j < R; j++) valid |= c.last_mask << (j * B);
-  const int nv = __popc(valid);
-  const uint32_t c0 = stash[0], c1 = stash[1], c2 = stash[2], z0 = stash[3];
-  const int D = 4 + ((kx > 1 || c.x_pbc) ? 1 : 0) + ((kx < c.Lx || c.x_pbc) ? 1 : 0);
-  const int n_old = __popc(c0 & valid) + 2 * __popc(c1 & valid) + 4 * __popc(c2 & valid);
-  const int n_fl = __popc(c0 & fl) + 2 * __popc(c1 & fl) + 4 * __popc(c2 & fl);
-  LayerSums r;
-  r.layer = kx - 1;
-  r.b = 2 * (n_old + D * __popc(fl) - 2 * n_fl) - D * nv;
-  r.m = 2 * (__popc(v & valid) + __popc(z0 & valid)) - 2 * nv;
-  return r;
-}
-
 // The R rows of a group, and, for the group holding ky = 1, then the group
 // holding ky = Ly of the wrap partner layer (fetched after the first group is
-// stored, as update_fetched does with single rows).  MEAS: the record sums of
-// both groups (the seam correction taken on the rows ky = 1 and ky = Ly).
-template <uint32_t R, bool FAST, bool MEAS, typename AccOf>
+// stored, as update_fetched does with single rows).  Plain launches only: the
+// summing launches take a group's rows one at a time (sweep_block_rows).
+template <uint32_t R, bool FAST>
 __device__ __forceinline__ void update_packed(const FilmCtx& c, const Packed& p, const uint32_t* s_thr,
-                                              const uint32_t* s_alw, uint32_t* stash, LayerSums* r1,
-                                              LayerSums* r2, AccOf acc_of) {
-  constexpr uint32_t B = 8 / R;
-  const uint32_t fl = decide_packed<R, FAST, MEAS>(c, p, s_thr, s_alw, stash);
-  const uint32_t v = p.S ^ fl;
-  store_packed<R>(c, p, v);
-  if (MEAS) *r1 = packed_sums<R>(c, p.kx, fl, v, stash);
+                                              const uint32_t* s_alw) {
+  const uint32_t fl = decide_packed<R, FAST>(c, p, s_thr, s_alw);
+  store_packed<R>(c, p, p.S ^ fl);
   if (p.ky0 != 1) return;
-  if (MEAS) {  // a pair lane adds its first group's sums now (its own atomics), not across the partner's draws
-    add_lane_sums(acc_of(), *r1);
-    r1->layer = 0xFFFFFFFFu;
-  }
   const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - p.kx) : p.kx;
   Packed g;
   fetch_packed<R>(c, kx2, c.Ly - R + 1, g);
-  if (MEAS) {
-    // rows ky = 1 (slot 0 of this group) and ky = Ly (slot R - 1 of g)
-    Fetched gl;
-    gl.S = (g.S >> ((R - 1) * B)) & slot_mask<R>();
-    gl.z0 = (g.z0 >> ((R - 1) * B)) & slot_mask<R>();
-    stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, 0, v & slot_mask<R>(), stash[3] & slot_mask<R>(), gl) : 0u;
-  }
-  const uint32_t fl2 = decide_packed<R, FAST, MEAS>(c, g, s_thr, s_alw, stash);
-  const uint32_t v2 = g.S ^ fl2;
-  store_packed<R>(c, g, v2);
-  if (MEAS) {
-    *r2 = packed_sums<R>(c, kx2, fl2, v2, stash);
-    r2->b += (int)stash[4];
-  }
+  const uint32_t fl2 = decide_packed<R, FAST>(c, g, s_thr, s_alw);
+  store_packed<R>(c, g, g.S ^ fl2);
 }
 
 // Group of packed update item `item`: the first Lx items are the groups
@@ -858,32 +815,19 @@ __device__ __forceinline__ void item_group(const FilmCtx& c, uint32_t item, uint
   ky0 = pair ? 1u : (r - q * (c.Ly / R - 2) + 1) * R + 1;
 }
 
-// The packed items of one block (as sweep_block's word items), one after
-// another: a packed group already holds R rows' loads in flight.
-template <uint32_t R, bool FAST, uint32_t ITEMS, bool MEAS, typename AccOf>
+// The packed items of one block (as sweep_block's word items) in a plain
+// launch.
+template <uint32_t R, bool FAST>
 __device__ __forceinline__ void sweep_block_packed(const FilmCtx& c, uint32_t first, uint32_t items, uint32_t dm,
                                                    uint32_t dl, const uint32_t* __restrict__ s_thr,
-                                                   const uint32_t* __restrict__ s_alw, bool meas, AccOf acc_of,
-                                                   uint32_t* stash) {
-#pragma unroll 1
-  for (uint32_t it = 0; it < ITEMS; it++) {
-    const uint32_t item = first + threadIdx.x + it * kFilmThreads;
-    const bool mine = item < items;
-    Packed p;
-    if (mine) {
-      uint32_t kx, ky0;
-      item_group<R>(c, item, dm, dl, kx, ky0);
-      fetch_packed<R>(c, kx, ky0, p);
-    }
-    LayerSums r1, r2;
-    if (MEAS && meas) {
-      if (mine) update_packed<R, FAST, true>(c, p, s_thr, s_alw, stash, &r1, &r2, acc_of);
-      add_layer_sums(acc_of(), r1);
-      add_lane_sums(acc_of(), r2);
-    } else if (mine) {
-      update_packed<R, FAST, false>(c, p, s_thr, s_alw, stash, &r1, &r2, acc_of);
-    }
-  }
+                                                   const uint32_t* __restrict__ s_alw) {
+  const uint32_t item = first + threadIdx.x;
+  if (item >= items) return;
+  uint32_t kx, ky0;
+  item_group<R>(c, item, dm, dl, kx, ky0);
+  Packed p;
+  fetch_packed<R>(c, kx, ky0, p);
+  update_packed<R, FAST>(c, p, s_thr, s_alw);
 }
 
 // The packed items of one block, each group's rows decided one at a time
@@ -983,8 +927,8 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
     // and exact-table launches, whose registers have no room for the packed
     // body, take the group's rows one after another
     if (FAST && !MEAS) {
-      if (c.pack == 4) sweep_block_packed<4, FAST, 1, MEAS>(c, first, items, dym, dyl, s_thr, s_alw, meas, acc_of, stash);
-      else sweep_block_packed<2, FAST, 1, MEAS>(c, first, items, dym, dyl, s_thr, s_alw, meas, acc_of, stash);
+      if (c.pack == 4) sweep_block_packed<4, FAST>(c, first, items, dym, dyl, s_thr, s_alw);
+      else sweep_block_packed<2, FAST>(c, first, items, dym, dyl, s_thr, s_alw);
     } else {
       sweep_block_rows<FAST, MEAS, PATHS4>(c, first, items, dym, dyl, s_thr, s_alw, meas, acc_of, stash);
     }
