@@ -11,7 +11,10 @@ final spins: a bit-exact match over the whole run.
     record (the benchmark's step), in the autotuned launch shape and in both
     grid shapes;
   - the 64-film integration set: all 64 films in one autotuned batch under
-    CUDA graphs, a record every sweep.
+    CUDA graphs, a record every sweep;
+  - the 40-film temperature scan: all 40 films in one batch for 10^4 sweeps
+    with a record every sweep, the coldest (T = 1.5) and hottest (T = 4.4)
+    against the oracle's digests of their whole runs.
 """
 import hashlib
 import json
@@ -103,4 +106,40 @@ def test_integration_set_full_run():
     for e in d["films"]:
         i = e["index"]
         check_film(e, b.read_series(i), b.get_spins(i), f"integration-set film {i}")
+    b.close()
+
+
+def test_temperature_scan_full_run():
+    """All 40 films of the temperature scan in one batch (the benchmark's
+    launch: autotuned, default lanes, CUDA graphs), 10^4 sweeps with a record
+    after every sweep.  The T = 1.5 and T = 4.4 films match the oracle's
+    digests over the whole run; for every fourth film the last record equals
+    the oracle's record of its final spins."""
+    from oracle import oracle as O
+    d = digests("t_scan_ends")
+    n = d["films"][0]["n_sweeps"]
+    assert n == 10000
+    recipe = WL.t_scan_40(n_sweeps=n)
+    ends = {e["index"]: e for e in d["films"]}
+    assert sorted(ends) == [0, len(recipe) - 1]
+    jobs = [dict(j) for j in recipe]
+    for i, e in ends.items():
+        jobs[i] = stored_jobs({"films": [dict(e, index=0)]}, [recipe[i]])[0]
+    b = ig.Batch(jobs)
+    b.autotune()
+    b.reserve_records(n)
+    b.sweep(n, True)
+    for i, e in ends.items():
+        check_film(e, b.read_series(i), b.get_spins(i), f"temperature-scan film {i} (T = {jobs[i]['T']})")
+    for i in range(0, len(jobs), 4):
+        j = jobs[i]
+        recs = b.read_series(i) if i not in ends else None
+        spins = b.get_spins(i)
+        o = O.Film(j["Lx"], j["Ly"], j["Lz"], j["J"], j["H1"], j["T"], j["seed"], y_mode=j["y_mode"],
+                   replica=j["replica"])
+        o.set_spins(spins)
+        o.sweep_count = n
+        if recs is not None:
+            assert recs.shape == (n, 5 + j["Lx"]), i
+            assert np.array_equal(recs[-1], o.measure()), i
     b.close()
