@@ -972,10 +972,17 @@ __device__ __forceinline__ void sweep_block(const FilmCtx& c, uint32_t first, ui
 // MODE kUpdAccumulate: the half-sweep 1 launch
 // of a sweep after which some film records; those films add their record
 // sums into their accumulators in `part`.  MODE kUpdWriteRecord: a half-sweep
-// 0 launch right after such a sweep; the first block of each film that
+// 0 launch right after such a sweep; the last block of each film that
 // recorded after `rec_done` sweeps writes that record (write_record) before
-// its update, so the write overlaps the launch's other blocks.
+// its update, so the write overlaps the launch's other blocks.  The last
+// block holds the film's ragged end, so it has the fewest words; the first
+// ones hold the pair items, whose threads also update the wrap partner.
 enum : uint32_t { kUpdPlain = 0, kUpdAccumulate = 1, kUpdWriteRecord = 2 };
+
+template <uint32_t ITEMS>
+__device__ __forceinline__ uint32_t last_update_block(const FilmDesc& d) {
+  return d.upd_block_begin + (grid_items(d, ITEMS) + words_per_block(ITEMS) - 1) / words_per_block(ITEMS) - 1;
+}
 
 template <bool FAST, uint32_t ITEMS, uint32_t MODE, bool PK = false>
 __global__ void __launch_bounds__(kFilmThreads, PK ? (MODE == kUpdAccumulate ? (FAST ? kMultiMinBlocks - 1
@@ -1021,7 +1028,7 @@ update_kernel(const FilmDesc* __restrict__ films, const uint32_t* __restrict__ o
     pdl_wait();
     if (threadIdx.x == 0) s_d.sweep = __ldcg(&films[f].sweep);
     __syncthreads();
-    if (MODE == kUpdWriteRecord && vb == s_d.upd_block_begin && records_after(s_d, s_d.sweep, rec_done))
+    if (MODE == kUpdWriteRecord && vb == last_update_block<ITEMS>(s_d) && records_after(s_d, s_d.sweep, rec_done))
       write_record(const_cast<FilmDesc*>(films + f), s_d, s_d.sweep, part, records, rec_done, s_red, &s_slot);
     if (s_d.sweep + k >= s_d.sweep_end) continue;
     FilmCtx c;
