@@ -147,6 +147,36 @@ def test_checkpoint_resume_is_bit_exact():
     h.close()
 
 
+@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2", "gridq"])
+def test_sweeps_up_to_the_counter_limit_are_bit_exact(shape):
+    """The sweep index is the third word of every Philox counter, and
+    0xFFFFFFFF is reserved for the initial state's draws.  A film resumed 40
+    sweeps before the limit runs 39 of them bit-exact (a record every 3
+    sweeps, so the records' sweep column passes 2^32 - 2); the 40th sweep is
+    refused before any device work, and the film carries on unchanged."""
+    case = (9, 8, 70, ig.Y_GAPBC, ig.X_FREE, 0.45, 0.0, 3.0, ig.INIT_SLAB_Y, 0.1)
+    g, o = _pair(case, seed=5, shape=shape)
+    g.sweep(3, 0)
+    o.sweep(3, 0)
+    start = 0xFFFFFFFF - 40
+    g.sweep_count = start
+    o.sweep_count = start
+    g.sweep(39, 3)
+    want = o.sweep(39, 3)
+    assert want[-1][0] == 0xFFFFFFFF - 1 - (0xFFFFFFFF - 1) % 3
+    assert np.array_equal(g.read_series(), want)
+    assert np.array_equal(g.get_spins(), o.get_spins())
+    with pytest.raises(ig.IsingError) as e:
+        g.sweep(1, 0)
+    assert e.value.status == ig.EINVAL
+    with pytest.raises(ValueError):
+        o.sweep(1, 0)
+    assert g.sweep_count == 0xFFFFFFFF - 1
+    assert np.array_equal(g.get_spins(), o.get_spins())
+    assert np.array_equal(g.measure(), o.measure())
+    g.close()
+
+
 def test_record_ring_grows_and_drains_in_order():
     case = (4, 5, 40, ig.Y_GAPBC, ig.X_FREE, 0.5, 0.0, 3.0, ig.INIT_RANDOM, 0.0)
     g, o = _pair(case)

@@ -104,3 +104,30 @@ def test_late_job_shares_chunks_with_a_running_job():
         assert np.array_equal(recs, want_r)
         assert np.array_equal(spins, want_s)
     srv.close()
+
+
+def test_single_sweep_jobs_and_zero_sweep_jobs():
+    """The smallest jobs: one sweep, recorded or not, beside a long one and
+    inside one chunk; they finish in the first chunk and still equal the
+    oracle's chain alone.  A job of no sweeps is refused at submission."""
+    base = dict(Lx=6, Ly=7, Lz=18, T=2.7, H1=0.3, seed=4, init_kind=ig.INIT_SLAB_Y, flip_p=0.02,
+                y_mode=ig.Y_GAPBC)
+    specs = [dict(base, replica=0, n_sweeps=1, measure_every=1),
+             dict(base, replica=1, n_sweeps=1, measure_every=0),
+             dict(base, replica=2, n_sweeps=90, measure_every=4),
+             dict(base, replica=3, n_sweeps=1, measure_every=2)]
+    srv = ig.Server(64 << 20, chunk_sweeps=16)
+    with pytest.raises(ig.IsingError) as e:
+        srv.submit([dict(base, replica=9, n_sweeps=0)])
+    assert e.value.status == ig.EINVAL
+    tickets = srv.submit(specs)
+    for t, sp in zip(tickets, specs):
+        srv.wait(t, 300.0)
+        recs, spins, info = srv.result(t)
+        want_r, want_s = _oracle(sp)
+        assert recs.shape == want_r.shape, t
+        assert np.array_equal(recs, want_r), t
+        assert np.array_equal(spins, want_s), t
+        if sp["n_sweeps"] == 1:
+            assert info["first_chunk"] == info["last_chunk"], t
+    srv.close()
