@@ -15,7 +15,7 @@ and, in plain numbers, the last record.
 
 Usage (each configuration writes its own file ``digests_<name>.json``):
   python tests/golden/make_config_digests.py film_46m            # 2000 sweeps, a record every 10
-  python tests/golden/make_config_digests.py ti_batch [sweeps]   # 64 films, a record every sweep
+  python tests/golden/make_config_digests.py ti_batch [sweeps]   # 64 films, 5000 sweeps, a record every sweep
   python tests/golden/make_config_digests.py t_scan_ends         # T = 1.5 and 4.4 films, 10^4 sweeps
 """
 from __future__ import annotations
@@ -75,7 +75,7 @@ def main(argv):
         todo = [(0, job, job["n_sweeps"], ncpu)]
         desc = "46M-site film 120x240x1600, T = 3, H1 = +0.55, slab start + 1% flips, seed 2, full run"
     elif name == "ti_batch":
-        n = int(argv[2]) if len(argv) > 2 else 500
+        n = int(argv[2]) if len(argv) > 2 else 5000
         jobs = WL.ti_batch(n_sweeps=n)
         todo = [(i, j, n, 1) for i, j in enumerate(jobs)]
         desc = f"64-film integration set, every film, {n} sweeps with a record every sweep"
