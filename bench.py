@@ -38,7 +38,7 @@ def alu_frac(attempts_per_ns):
 
 
 SHAPE_NAMES = {0: "auto", 1: "resident", 2: "grid, 1 word/thread", 3: "grid, 2 words/thread",
-               4: "grid, 4 threads/word"}
+               4: "grid, 4 threads/word", 5: "cluster-resident"}
 SHAPE_FLAGS = {1: "resident", 2: "grid1", 3: "grid2", 4: "gridq"}
 METRIC = "spin-flip attempts/ns on 1 GB300, batched vs plain, % roofline; p99 latency"
 UNIT = "attempts/ns"
@@ -382,6 +382,8 @@ def procedures(ig, WL):
         dt = time.perf_counter() - t0
         recs = [b.read_series(i) for i in range(len(wl["jobs"]))]
         lanes = b.lanes
+        if shape == SHAPE_NAMES[5]:
+            shape += f", {b.cluster_size} CTAs per film"
         b.close()
         att = sum(WL.sites(j) for j in wl["jobs"]) * wl["n_sweeps"]
         return recs, {"films": len(wl["jobs"]), "attempts": att, "sweep_s": dt, "attempts_per_ns": att / dt / 1e9,
@@ -442,14 +444,18 @@ def profile_set(args):
     if args.profile_every is not None:
         jobs = [dict(j, measure_every=args.profile_every) for j in jobs]
     b = ig.Batch(jobs, lanes=args.profile_lanes)
-    b.set_shape({"grid1": ig.SHAPE_GRID_1, "grid2": ig.SHAPE_GRID_2, "gridq": ig.SHAPE_GRID_Q}[args.profile_shape])
+    if args.profile_shape == "cluster":
+        b.set_cluster_size(args.profile_cluster)
+    b.set_shape({"grid1": ig.SHAPE_GRID_1, "grid2": ig.SHAPE_GRID_2, "gridq": ig.SHAPE_GRID_Q,
+                 "cluster": ig.SHAPE_CLUSTER}[args.profile_shape])
+    cl = f" ({b.cluster_size} CTAs per film)" if args.profile_shape == "cluster" else ""
     if args.profile_every != 0:
         b.reserve_records(n)
     b.sweep(n, False)
     b.synchronize()
     lanes = b.lanes
     b.close()
-    print(f"{args.profile_set}: {len(jobs)} films in {lanes} lane(s), {n} sweeps, shape {args.profile_shape}, "
+    print(f"{args.profile_set}: {len(jobs)} films in {lanes} lane(s), {n} sweeps, shape {args.profile_shape}{cl}, "
           f"records every {jobs[0]['measure_every']} sweeps")
 
 
@@ -498,7 +504,9 @@ def main():
                          "pins the autotuner's normal pick because ncu's serialisation distorts its timing")
     ap.add_argument("--profile-set", choices=PROFILE_SETS,
                     help="run one film set for ncu (see profile_set) instead of the benchmark")
-    ap.add_argument("--profile-shape", default="grid2", choices=["grid1", "grid2", "gridq"])
+    ap.add_argument("--profile-shape", default="grid2", choices=["grid1", "grid2", "gridq", "cluster"])
+    ap.add_argument("--profile-cluster", type=int, default=0,
+                    help="CTAs per film of --profile-shape cluster (0: the library's automatic size)")
     ap.add_argument("--profile-sweeps", type=int, default=4)
     ap.add_argument("--profile-every", type=int, default=None, help="record interval (0: no records)")
     ap.add_argument("--profile-lanes", type=int, default=1, help="batch lanes (0: the library's default)")

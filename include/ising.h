@@ -83,11 +83,18 @@ enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
  * GRID_Q    the same with four threads per word, each drawing two of its
  *           eight Philox calls: four times the threads for the same work,
  *           for films too small to fill the GPU otherwise.
+ * CLUSTER   (batches only) one thread-block cluster of C CTAs per film
+ *           keeps the film in distributed shared memory for a whole
+ *           ising_batch_sweep call, CTA r holding layers [r Lx / C,
+ *           (r+1) Lx / C) of both parity planes; a cluster barrier separates
+ *           the half-sweeps, so films never wait for one another and no
+ *           launch boundary falls between half-sweeps (the Appendix's many
+ *           independent films, each on its own few SMs).
  * AUTO      the autotuner's measurement for this film shape and record
  *           interval if there is one, else RESIDENT up to 32768 spins and
  *           GRID_1 above. */
 enum { ISING_SHAPE_AUTO = 0, ISING_SHAPE_RESIDENT = 1, ISING_SHAPE_GRID_1 = 2, ISING_SHAPE_GRID_2 = 3,
-       ISING_SHAPE_GRID_Q = 4 };
+       ISING_SHAPE_GRID_Q = 4, ISING_SHAPE_CLUSTER = 5 };
 
 typedef struct ising ising;
 
@@ -253,17 +260,31 @@ int ising_batch_sweep(ising_batch *b, uint64_t n_sweeps, int use_graph);
  * grown before the refusal keep their larger rings). */
 int ising_batch_reserve_records(ising_batch *b, uint64_t n_records);
 
-/* Launch shape of the batch's grid kernels: GRID_1, GRID_2, GRID_Q, or AUTO (the
+/* Launch shape of the batch: GRID_1, GRID_2, GRID_Q, CLUSTER, or AUTO (the
  * autotuner's choice once ising_batch_autotune has run, else GRID_1).
+ * CLUSTER takes the pinned cluster size (ising_batch_set_cluster_size), else
+ * the largest C <= 8 for which every film qualifies and the n films' n C CTAs
+ * fit on the GPU's SMs (C = 1 when the films outnumber the SMs); a film
+ * qualifies for C when Lx >= C and a CTA's slab of ceil(Lx / C) layers (two
+ * planes of Ly W 32-bit words each, W = ceil(Lz / 64)) plus 24 Lx bytes of
+ * tables fits in 200 KiB of shared memory.  EINVAL when none qualifies.
  * RESIDENT is EINVAL for a batch.  Changing it drops the captured graphs. */
 int ising_batch_set_shape(ising_batch *b, int shape);
 int ising_batch_get_shape(ising_batch *b, int *shape);
+/* CTAs per film of the CLUSTER shape: 1..8, or 0 for the automatic choice
+ * above.  EINVAL if > 8 or some film does not qualify (nothing changes).
+ * Takes effect at once when the batch is on CLUSTER.  get: the size the
+ * batch runs with now, 0 when it is on a grid shape. */
+int ising_batch_set_cluster_size(ising_batch *b, uint32_t cluster_size);
+int ising_batch_get_cluster_size(const ising_batch *b, uint32_t *cluster_size);
 
-/* Autotuner: times GRID_1, GRID_2 and GRID_Q on a scratch batch of the same jobs
- * in the same lanes (from their initial states; the kernels' work does not
- * depend on the spins), all lanes running, graph replay and records
- * included, and adopts the faster for every lane unless a shape is pinned;
- * *shape (may be NULL) receives it.  Synchronises. */
+/* Autotuner: times GRID_1, GRID_2, GRID_Q and CLUSTER at every cluster size
+ * for which all films qualify and their clusters fit on the GPU at once, on a
+ * scratch batch of the same jobs in the same lanes (from their initial
+ * states; the kernels' work does not depend on the spins), all lanes
+ * running, graph replay and records included, and adopts the fastest for
+ * every lane unless a shape is pinned; *shape (may be NULL) receives it.
+ * Synchronises. */
 int ising_batch_autotune(ising_batch *b, int *shape);
 
 /* Per-film accessors (index i < n).  Host buffers; synchronise. */

@@ -7,6 +7,6 @@ behind the C ABI of ``include/ising.h``; this package is the ctypes binding
 """
 from .binding import (  # noqa: F401
     EBUSY, ECUDA, EINVAL, ENOMEM, ENOTFOUND, ETIMEOUT, INIT_ALL_UP, INIT_RANDOM, INIT_SLAB_Y, MAX_LANES, OK, SHAPE_AUTO,
-    SHAPE_GRID_1, SHAPE_GRID_2, SHAPE_GRID_Q, SHAPE_RESIDENT, X_FREE, X_PBC, Y_APBC, Y_GAPBC, Y_PBC, Batch, Film, IsingError,
+    SHAPE_CLUSTER, SHAPE_GRID_1, SHAPE_GRID_2, SHAPE_GRID_Q, SHAPE_RESIDENT, X_FREE, X_PBC, Y_APBC, Y_GAPBC, Y_PBC, Batch, Film, IsingError,
     Server, check, check_counters, gauss_legendre, lib, make_jobs, series_energy, series_mean, ti_beta_trapezoid,
     ti_surface_field, ti_temperature_trapezoid)

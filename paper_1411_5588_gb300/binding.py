@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = range(7)
 Y_GAPBC, Y_PBC, Y_APBC = 0, 1, 2
 X_FREE, X_PBC = 0, 1
 INIT_RANDOM, INIT_SLAB_Y, INIT_ALL_UP = 0, 1, 2
-SHAPE_AUTO, SHAPE_RESIDENT, SHAPE_GRID_1, SHAPE_GRID_2, SHAPE_GRID_Q = 0, 1, 2, 3, 4
+SHAPE_AUTO, SHAPE_RESIDENT, SHAPE_GRID_1, SHAPE_GRID_2, SHAPE_GRID_Q, SHAPE_CLUSTER = 0, 1, 2, 3, 4, 5
 MAX_LANES = 16  # ISING_MAX_LANES
 
 _c = ctypes
@@ -71,6 +71,8 @@ _SIGS = {
     "ising_autotune": [P, _c.c_uint32, _c.POINTER(_c.c_int)],
     "ising_batch_set_shape": [P, _c.c_int],
     "ising_batch_get_shape": [P, _c.POINTER(_c.c_int)],
+    "ising_batch_set_cluster_size": [P, _c.c_uint32],
+    "ising_batch_get_cluster_size": [P, U32P],
     "ising_batch_autotune": [P, _c.POINTER(_c.c_int)],
     "ising_set_params": [P, _c.c_double, _c.c_double, _c.c_double],
     "ising_set_stream": [P, P],
@@ -384,8 +386,18 @@ class Batch:
         check(lib().ising_batch_get_shape(self._h, _c.byref(v)), "ising_batch_get_shape")
         return v.value
 
+    def set_cluster_size(self, cluster_size):
+        """CTAs per film of the CLUSTER shape (0: automatic)."""
+        check(lib().ising_batch_set_cluster_size(self._h, int(cluster_size)), "ising_batch_set_cluster_size")
+
+    @property
+    def cluster_size(self):
+        v = _c.c_uint32()
+        check(lib().ising_batch_get_cluster_size(self._h, _c.byref(v)), "ising_batch_get_cluster_size")
+        return int(v.value)
+
     def autotune(self):
-        """Time GRID_1 and GRID_2 on a scratch batch; adopts and returns the faster."""
+        """Time the grid shapes and the cluster sizes on a scratch batch; adopts and returns the fastest."""
         v = _c.c_int()
         check(lib().ising_batch_autotune(self._h, _c.byref(v)), "ising_batch_autotune")
         return v.value

@@ -13,6 +13,7 @@
 #include <map>
 #include <new>
 #include <numeric>
+#include <vector>
 
 #include "ising_host.h"
 
@@ -32,6 +33,10 @@ struct Lane {
   bool dirty = true;
   std::map<uint32_t, cudaGraphExec_t> graphs;  // chunk length -> executable graph
   cudaEvent_t ev_done = nullptr;               // the lane's last sweep call has finished
+  // cluster-resident path (CTAs per film; 0: the grid kernels), with the
+  // launch's shared memory and threads per CTA and its table variant
+  uint32_t cl_size = 0, cl_per_sm = 1, cl_smem = 0, cl_threads = 0;
+  bool cl_exact = false;
 
   void drop_graphs() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
@@ -119,6 +124,57 @@ int lane_apply_items(Lane* b, uint32_t items) {
   b->fs.layout();
   b->dirty = true;
   b->drop_graphs();
+  return ISING_OK;
+}
+
+// Launch parameters of the cluster path with C CTAs per film, per_sm CTAs per
+// SM, for every film of the lane; EINVAL if some film does not qualify.
+int lane_cluster_params(const Lane* b, uint32_t C, uint32_t per_sm, uint32_t* smem, uint32_t* threads, bool* exact) {
+  *smem = 0;
+  *threads = 0;
+  *exact = false;
+  for (const FilmDesc& d : b->fs.h) *exact = *exact || d.has_never != 0;
+  for (const FilmDesc& d : b->fs.h) {
+    const uint32_t m = cluster_smem_bytes(d, C);
+    if (m == 0) return fail(ISING_EINVAL, "film %ux%ux%u does not fit clusters of %u CTAs", d.Lx, d.Ly, d.Lz, C);
+    *smem = std::max(*smem, m);
+    *threads = std::max(*threads, cluster_threads(d, C, *exact, per_sm));
+  }
+  return ISING_OK;
+}
+
+// Switch the lane to the cluster path with C CTAs per film, per_sm per SM
+// (C = 0: back to the grid kernels).
+int lane_apply_cluster(Lane* b, uint32_t C, uint32_t per_sm) {
+  uint32_t smem = 0, threads = 0;
+  bool exact = false;
+  if (C) {
+    int rc = lane_cluster_params(b, C, per_sm, &smem, &threads, &exact);
+    if (rc) return rc;
+  }
+  if (b->cl_size == C && (C == 0 || b->cl_per_sm == per_sm)) return ISING_OK;
+  ISG_CK(cudaStreamSynchronize(b->fs.stream));
+  b->cl_size = C;
+  b->cl_per_sm = per_sm;
+  b->cl_smem = smem;
+  b->cl_threads = threads;
+  b->cl_exact = exact;
+  b->drop_graphs();
+  return ISING_OK;
+}
+
+// n sweeps of every film on the cluster path, in launches of at most 4096
+// sweeps; each launch advances the films' counters on the device.
+int lane_cluster_sweeps(Lane* b, uint64_t n) {
+  FilmSet& fs = b->fs;
+  while (n) {
+    const uint32_t k = (uint32_t)std::min<uint64_t>(n, 4096);
+    ISG_CK(launch_cluster(fs.L.films, (uint32_t)fs.h.size(), b->cl_size, b->cl_per_sm, b->cl_smem, b->cl_threads,
+                          b->cl_exact, fs.pool, fs.rec, k, fs.stream));
+    for (auto& d : fs.h) d.sweep += k;
+    b->sweeps += k;
+    n -= k;
+  }
   return ISING_OK;
 }
 
@@ -227,7 +283,9 @@ int lane_sweep(Lane* b, uint64_t n, int use_graph) {
   if (rc) return rc;
   if (G == 1) G = 64;
   while (G < 16) G *= 2;
-  if (!use_graph || G > 4096 || n < 2 * G) {
+  if (b->cl_size) {
+    rc = lane_cluster_sweeps(b, n);  // one launch holds every sweep: nothing to capture
+  } else if (!use_graph || G > 4096 || n < 2 * G) {
     rc = lane_direct_sweeps(b, (uint32_t)n);
   } else {
     const uint64_t prefix = (G - b->sweeps % G) % G;
@@ -296,6 +354,8 @@ struct ising_batch {
   int device = 0;
   int shape = ISING_SHAPE_AUTO;  // pinned launch shape, or AUTO
   int tuned_shape = 0;           // ising_batch_autotune's choice (0: none yet)
+  uint32_t cl_pinned = 0;        // CTAs per film pinned for the CLUSTER shape (0: automatic)
+  uint32_t tuned_cl = 0;         // the autotuner's CTAs per film when it chose CLUSTER
 
   cudaStream_t stream() const { return lanes[0]->fs.stream; }
   Lane* lane_of(size_t i) const { return lanes[where[i].first]; }
@@ -306,10 +366,50 @@ namespace {
 
 int batch_apply_items(ising_batch* b, uint32_t items) {
   for (Lane* l : b->lanes) {
-    int rc = lane_apply_items(l, items);
+    int rc = lane_apply_cluster(l, 0, 1);
+    if (!rc) rc = lane_apply_items(l, items);
     if (rc) return rc;
   }
   return ISING_OK;
+}
+
+// CTAs per SM of the cluster path with C CTAs per film: as many as the
+// batch's n C CTAs need to be resident at once, at most kClusterMaxPerSm.
+uint32_t batch_cluster_per_sm(const ising_batch* b, uint32_t C) {
+  const uint64_t n_sm = (uint64_t)std::max(1, b->lanes[0]->fs.n_sm);
+  const uint64_t k = ((uint64_t)b->jobs.size() * C + n_sm - 1) / n_sm;
+  return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(k, 1), kClusterMaxPerSm);
+}
+
+// Every lane on the cluster path with C CTAs per film; on EINVAL (some film
+// does not qualify) every lane is back on the grid kernels.
+int batch_apply_cluster(ising_batch* b, uint32_t C) {
+  const uint32_t per_sm = batch_cluster_per_sm(b, C);
+  for (Lane* l : b->lanes) {
+    int rc = lane_apply_cluster(l, C, per_sm);
+    if (rc) {
+      for (Lane* m : b->lanes) lane_apply_cluster(m, 0, 1);
+      return rc;
+    }
+  }
+  return ISING_OK;
+}
+
+// CTAs per film of the CLUSTER shape when none is pinned: the most (up to
+// kClusterMaxSize) for which every film qualifies and all films' clusters fit
+// on the GPU's SMs at once, one CTA each; 1 when the films outnumber the
+// SMs; 0 when no size qualifies.
+uint32_t batch_auto_cluster(const ising_batch* b) {
+  const size_t nf = b->jobs.size();
+  const size_t n_sm = (size_t)std::max(1, b->lanes[0]->fs.n_sm);
+  for (uint32_t C = kClusterMaxSize; C >= 1; C--) {
+    if (C > 1 && nf * C > n_sm) continue;
+    bool ok = true;
+    for (const Lane* l : b->lanes)
+      for (const FilmDesc& d : l->fs.h) ok = ok && cluster_smem_bytes(d, C) != 0;
+    if (ok) return C;
+  }
+  return 0;
 }
 
 int batch_sweep(ising_batch* b, uint64_t n, int use_graph) {
@@ -436,9 +536,17 @@ int ising_batch_set_shape(ising_batch* b, int shape) {
   clear_error();
   if (!b) return fail(ISING_EINVAL, "NULL batch");
   if (shape != ISING_SHAPE_AUTO && shape != ISING_SHAPE_GRID_1 && shape != ISING_SHAPE_GRID_2 &&
-      shape != ISING_SHAPE_GRID_Q)
-    return fail(ISING_EINVAL, "batches take AUTO, GRID_1, GRID_2 or GRID_Q");
+      shape != ISING_SHAPE_GRID_Q && shape != ISING_SHAPE_CLUSTER)
+    return fail(ISING_EINVAL, "batches take AUTO, GRID_1, GRID_2, GRID_Q or CLUSTER");
+  if (shape == ISING_SHAPE_CLUSTER) {
+    const uint32_t C = b->cl_pinned ? b->cl_pinned : batch_auto_cluster(b);
+    if (C == 0) return fail(ISING_EINVAL, "some film of the batch fits no cluster size");
+    int rc = batch_apply_cluster(b, C);
+    if (!rc) b->shape = shape;
+    return rc;
+  }
   b->shape = shape;
+  if (shape == ISING_SHAPE_AUTO && b->tuned_shape == ISING_SHAPE_CLUSTER) return batch_apply_cluster(b, b->tuned_cl);
   const uint32_t items = shape == ISING_SHAPE_AUTO ? (b->tuned_shape ? shape_items(b->tuned_shape) : 1u)
                                                    : shape_items(shape);
   return batch_apply_items(b, items);
@@ -447,7 +555,32 @@ int ising_batch_set_shape(ising_batch* b, int shape) {
 int ising_batch_get_shape(ising_batch* b, int* shape) {
   clear_error();
   if (!b || !shape) return fail(ISING_EINVAL, "NULL argument");
-  *shape = items_shape(b->lanes[0]->fs.items);
+  *shape = b->lanes[0]->cl_size ? ISING_SHAPE_CLUSTER : items_shape(b->lanes[0]->fs.items);
+  return ISING_OK;
+}
+
+int ising_batch_set_cluster_size(ising_batch* b, uint32_t cluster_size) {
+  clear_error();
+  if (!b) return fail(ISING_EINVAL, "NULL batch");
+  if (cluster_size > kClusterMaxSize) return fail(ISING_EINVAL, "clusters hold at most %u CTAs", kClusterMaxSize);
+  if (cluster_size) {  // every film must qualify before anything changes
+    uint32_t smem, threads;
+    bool exact;
+    for (Lane* l : b->lanes) {
+      int rc = lane_cluster_params(l, cluster_size, 1, &smem, &threads, &exact);
+      if (rc) return rc;
+    }
+  }
+  b->cl_pinned = cluster_size;
+  if (b->lanes[0]->cl_size && b->shape == ISING_SHAPE_CLUSTER)
+    return batch_apply_cluster(b, cluster_size ? cluster_size : batch_auto_cluster(b));
+  return ISING_OK;
+}
+
+int ising_batch_get_cluster_size(const ising_batch* b, uint32_t* cluster_size) {
+  clear_error();
+  if (!b || !cluster_size) return fail(ISING_EINVAL, "NULL argument");
+  *cluster_size = b->lanes[0]->cl_size;
   return ISING_OK;
 }
 
@@ -468,9 +601,33 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(ISING_ECUDA, "event creation failed");
   int best = ISING_SHAPE_GRID_1;
+  uint32_t best_cl = 0;
   float best_ms = 3.0e38f;
-  for (int cand = ISING_SHAPE_GRID_1; !rc && cand <= ISING_SHAPE_GRID_Q; cand++) {
-    rc = batch_apply_items(s, shape_items(cand));
+  // grid shapes, then the cluster path at each cluster size whose clusters
+  // all fit on the GPU at once (or 1 CTA per film when the films outnumber
+  // the SMs) and for which every film qualifies
+  std::vector<std::pair<int, uint32_t>> cands = {
+      {ISING_SHAPE_GRID_1, 0}, {ISING_SHAPE_GRID_2, 0}, {ISING_SHAPE_GRID_Q, 0}};
+  {
+    const size_t nf = b->jobs.size();
+    const size_t n_sm = (size_t)std::max(1, b->lanes[0]->fs.n_sm);
+    for (uint32_t C = 1; C <= kClusterMaxSize; C++) {
+      if (C > 1 && nf * C > kClusterMaxPerSm * n_sm) break;
+      const uint32_t per_sm = batch_cluster_per_sm(b, C);
+      bool ok = true;
+      for (const Lane* l : b->lanes) {
+        uint32_t smem = 0, threads = 0;
+        bool exact = false;
+        ok = ok && lane_cluster_params(l, C, per_sm, &smem, &threads, &exact) == ISING_OK &&
+             cluster_capacity(C, per_sm, smem, threads, exact) > 0;
+      }
+      clear_error();
+      if (ok) cands.push_back({ISING_SHAPE_CLUSTER, C});
+    }
+  }
+  for (size_t ci = 0; !rc && ci < cands.size(); ci++) {
+    const int cand = cands[ci].first;
+    rc = cand == ISING_SHAPE_CLUSTER ? batch_apply_cluster(s, cands[ci].second) : batch_apply_items(s, shape_items(cand));
     float ms = 3.0e38f;
     for (int rep = 0; !rc && rep < 3; rep++) {  // the first run captures the graphs
       if (cudaEventRecord(e0, s->stream()) != cudaSuccess) rc = fail(ISING_ECUDA, "event record failed");
@@ -486,6 +643,7 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
     if (!rc && ms < kTuneMargin * best_ms) {  // a later shape must win clearly
       best_ms = ms;
       best = cand;
+      best_cl = cands[ci].second;
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -493,7 +651,9 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   ising_batch_destroy(s);
   if (rc) return rc;
   b->tuned_shape = best;
-  if (b->shape == ISING_SHAPE_AUTO) rc = batch_apply_items(b, shape_items(best));
+  b->tuned_cl = best_cl;
+  if (b->shape == ISING_SHAPE_AUTO)
+    rc = best == ISING_SHAPE_CLUSTER ? batch_apply_cluster(b, best_cl) : batch_apply_items(b, shape_items(best));
   if (!rc && shape) *shape = best;
   return rc;
 }

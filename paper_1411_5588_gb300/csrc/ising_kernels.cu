@@ -15,8 +15,10 @@
 //    lattice alone (an on-demand measurement), per-block partials in a
 //    scratch area, then one block per film writes the record.
 //  - init_kernel, pack_kernel, unpack_kernel, advance_kernel.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "ising_device.cuh"
@@ -24,6 +26,8 @@
 #include "ising_launch.h"
 
 namespace isg {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -1382,6 +1386,295 @@ resident_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64
   }
 }
 
+// ------------------------------------------------------------- cluster-resident path
+
+// Films held in distributed shared memory.  One thread-block cluster of C
+// CTAs keeps one film for every sweep of a call: CTA r holds layers
+// kx - 1 in [r Lx / C, (r + 1) Lx / C) of both planes (row stride W), and
+// the cluster barrier between half-sweeps is the only synchronisation, so
+// films never wait for one another and no launch boundary falls between
+// half-sweeps.  A word's x-neighbour layer across a slab boundary, and the
+// mirrored layer of an Eq. 11 partner row, sit in a peer CTA: every access
+// goes through a table of the generic addresses of all layers of the film
+// (the own CTA's shared window, or a peer's mapped into the cluster window),
+// so such a word is a distributed-shared-memory load, and the partner's
+// update a remote store.  Within a half-sweep no word is read that another
+// thread writes (the checkerboard; the partner row reads the ky = 1 word its
+// own thread has just written), so plain loads suffice, and the barrier's
+// release/acquire orders one half-sweep's stores before the next one's loads.
+
+// The words of fetch_word for word w of row (kx, ky), from the layer table
+// lp[X * Lx + kx - 1] (plane X, 0-based layer kx - 1).
+__device__ __forceinline__ void fetch_word_cl(const FilmCtx& c, uint32_t* const* lp, uint32_t kx, uint32_t ky,
+                                              uint32_t w, Fetched& f) {
+  const uint32_t Lx = c.Lx, Ly = c.Ly, W = c.W;
+  const uint32_t X = (kx + ky + 1 + c.colour) & 1u;
+  uint32_t* const* LP = lp + X * Lx;
+  uint32_t* const* LQ = lp + (X ^ 1u) * Lx;
+  const uint32_t rbase = (ky - 1) * W, base = rbase + w;
+  const uint32_t lim = Ly * W;  // words of one layer
+  const uint32_t* P = LP[kx - 1];
+  const uint32_t* Q = LQ[kx - 1];
+  const uint32_t gkx = (c.y_mode == kYGapbc) ? (Lx - kx) : (kx - 1);  // 0-based layer of the wrap row
+  f.kx = kx; f.ky = ky; f.w = w;
+  f.S = ISG_LD(P, base, lim, 61);
+  f.xm = (kx > 1) ? ISG_LD(LP[kx - 2], base, lim, 62) : (c.x_pbc ? ISG_LD(LP[Lx - 1], base, lim, 63) : 0u);
+  f.xp = (kx < Lx) ? ISG_LD(LP[kx], base, lim, 64) : (c.x_pbc ? ISG_LD(LP[0], base, lim, 65) : 0u);
+  f.ym = (ky > 1) ? ISG_LD(P, base - W, lim, 66) : ISG_LD(LP[gkx], (Ly - 1) * W + w, lim, 67);
+  f.yp = (ky < Ly) ? ISG_LD(P, base + W, lim, 68) : ISG_LD(LP[gkx], w, lim, 69);
+  f.z0 = ISG_LD(Q, base, lim, 70);
+  if (X == 0)  // previous word, or the row's last
+    f.za = (w > 0) ? ISG_LD(Q, base - 1, lim, 71) : ISG_LD(Q, rbase + W - 1, lim, 72);
+  else  // next word, or the row's first
+    f.za = (w + 1 < W) ? ISG_LD(Q, base + 1, lim, 73) : ISG_LD(Q, rbase, lim, 74);
+  f.zf = ISG_LD(Q, rbase, lim, 75);
+}
+
+__device__ __forceinline__ void store_word_cl(const FilmCtx& c, uint32_t* const* lp, const Fetched& f, uint32_t v) {
+  const uint32_t X = (f.kx + f.ky + 1 + c.colour) & 1u;
+  ISG_ST(lp[X * c.Lx + f.kx - 1], (f.ky - 1) * c.W + f.w, c.Ly * c.W, 76, v);
+}
+
+// update_fetched over the layer table.
+template <bool FAST, bool MEAS>
+__device__ __forceinline__ void update_fetched_cl(const FilmCtx& c, uint32_t* const* lp, const Fetched& f,
+                                                  const uint32_t* s_thr, const uint32_t* s_alw,
+                                                  uint32_t* stash = nullptr, LayerSums* r1 = nullptr,
+                                                  LayerSums* r2 = nullptr) {
+  const uint32_t fl = decide_any<FAST, false, MEAS, true>(c, f, s_thr, s_alw, 0, stash);
+  const uint32_t v = f.S ^ fl;
+  store_word_cl(c, lp, f, v);
+  if (MEAS) *r1 = word_sums(c, f.kx, f.w, fl, v, stash);
+  if (f.ky == 1) {
+    const uint32_t kx2 = (c.y_mode == kYGapbc) ? (c.Lx + 1 - f.kx) : f.kx;
+    Fetched g;
+    fetch_word_cl(c, lp, kx2, c.Ly, f.w, g);
+    if (MEAS) stash[4] = c.seam_same ? (uint32_t)seam_adjust(c, f.w, v, stash[3], g) : 0u;
+    const uint32_t fl2 = decide_any<FAST, false, MEAS, true>(c, g, s_thr, s_alw, 0, stash);
+    const uint32_t v2 = g.S ^ fl2;
+    store_word_cl(c, lp, g, v2);
+    if (MEAS) {
+      *r2 = word_sums(c, kx2, g.w, fl2, v2, stash);
+      r2->b += (int)stash[4];
+    }
+  }
+}
+
+// Word of the CTA's update item `item`: its nl layers from layer a + 1 on,
+// the ky = 1 words first (their threads also update the wrap partner), then
+// rows ky = 2 .. Ly-1 layer by layer (item_word on a slab of layers).
+__device__ __forceinline__ void slab_item_word(const FilmDesc& d, uint32_t a, uint32_t nl, uint32_t item,
+                                               uint32_t& kx, uint32_t& ky, uint32_t& w) {
+  const uint32_t rp = fastdiv(item, d.divw_m, d.divw_l);
+  w = item - rp * d.W;
+  const bool pair = rp < nl;
+  const uint32_t rq = pair ? 0u : rp - nl;
+  const uint32_t q = fastdiv(rq, d.divy_m, d.divy_l);
+  kx = a + (pair ? rp : q) + 1;
+  ky = pair ? 1u : rq - q * (d.Ly - 2) + 2;
+}
+
+// Rounds of a CTA's half-sweep: a pair item (a ky = 1 word and its wrap
+// partner) is two words of work, so its thread spends two rounds on it and
+// takes one regular item fewer, and no warp runs a round longer than the
+// others.  With P = q T + s pair items over T threads, thread t draws pair
+// items t, t + T, ... (q + [t < s] of them) in rounds 0, 2, ..., and the
+// P' regular items fill the remaining (thread, round) slots round by round:
+// R = max(2 ceil(P / T), ceil((P' + 2 P) / T)) rounds hold them all.
+struct SlabRounds {
+  uint32_t P, q, s, R;
+};
+
+__device__ __forceinline__ SlabRounds slab_rounds(uint32_t P, uint32_t P2, uint32_t T) {
+  SlabRounds o;
+  o.P = P;
+  o.q = P / T;
+  o.s = P - o.q * T;
+  const uint32_t rp = 2 * ((P + T - 1) / T), rw = (P2 + 2 * P + T - 1) / T;
+  o.R = rp > rw ? rp : rw;
+  return o;
+}
+
+// Item of thread t in round j: the pair item's index (< P) at the round that
+// starts it, 0xFFFFFFFF at the round its partner takes, else P + the regular
+// item's index (which may be >= P + P': nothing to do).
+__device__ __forceinline__ uint32_t slab_round_item(const SlabRounds& r, uint32_t t, uint32_t j, uint32_t T) {
+  const uint32_t kt = r.q + (t < r.s ? 1u : 0u);  // this thread's pair items
+  if (j < 2 * kt) return (j & 1u) ? 0xFFFFFFFFu : t + (j >> 1) * T;
+  const uint32_t j0 = 2 * r.q;
+  const uint32_t reg = (j < j0 + 2) ? (j - j0) * (T - r.s) + (t - r.s) : 2 * (T - r.s) + (j - j0 - 2) * T + t;
+  return r.P + reg;
+}
+
+// The record of sweep t (records-ring slot `slot`) from the layer sums the
+// cluster's CTAs left in buffer `buf`: this CTA writes m(kx) of its own
+// layers [a, b), rank 0 the totals.
+__device__ __forceinline__ void cluster_record(cg::cluster_group& cl, const FilmDesc& d, int64_t* records, int* s_m,
+                                               int (*s_tot)[2], uint32_t buf, uint32_t a, uint32_t b, uint32_t C,
+                                               uint32_t t, uint32_t slot) {
+  const uint32_t Lx = d.Lx;
+  int64_t* rec = records + d.rec_off + (size_t)slot * (5 + Lx);
+  for (uint32_t kx = a + threadIdx.x; kx < b; kx += blockDim.x) {
+    int v = 0;
+    for (uint32_t q = 0; q < C; q++) v += cl.map_shared_rank(s_m + buf * Lx, q)[kx];
+    rec[5 + kx] = v;
+    if (kx == 0) rec[3] = v;
+    if (kx == Lx - 1) rec[4] = v;
+  }
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    int B = 0, M = 0;
+    for (uint32_t q = 0; q < C; q++) {
+      const int* p = cl.map_shared_rank(&s_tot[buf][0], q);
+      B += p[0];
+      M += p[1];
+    }
+    rec[0] = (int64_t)t;
+    rec[1] = B;
+    rec[2] = M;
+  }
+}
+
+// n_sweeps sweeps of film blockIdx.x / C (C = the cluster's size), records
+// into its ring, sweep and rec_next advanced at the end.  Dynamic shared
+// memory: planes [2][ceil(Lx / C)][Ly][W] words, the layer table (2 Lx
+// generic addresses), and two buffers of Lx layer sums.
+template <bool FAST>
+__global__ void __launch_bounds__(cluster_max_threads(!FAST), 1)
+cluster_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64_t* __restrict__ records,
+               uint32_t n_sweeps) {
+  extern __shared__ __align__(16) uint32_t s_dyn[];
+  constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
+  __shared__ __align__(16) FilmDesc s_d;
+  __shared__ __align__(16) uint32_t s_thr[64];
+  __shared__ __align__(16) uint32_t s_alw[64];
+  __shared__ uint32_t s_stash[kStashSlots * kClusterThreads];
+  __shared__ int s_tot[2][2];  // {B, M} of the record being summed, two buffers
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t C = cl.num_blocks();
+  const uint32_t r = cl.block_rank();
+  FilmDesc* Fg = films + blockIdx.x / C;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Fg);
+    uint4* dst = reinterpret_cast<uint4*>(&s_d);
+    for (uint32_t i = threadIdx.x; i < kDescWords / 4; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
+    const bool al = (s_d.always[i >> 4] >> (i & 15)) & 1u;
+    s_thr[i] = FAST ? (al ? 0xFFFFFFFFu : s_d.thr[i >> 4][i & 15] - 1u) : s_d.thr[i >> 4][i & 15];
+    s_alw[i] = al ? 0xFFFFFFFFu : 0u;
+  }
+  if (!s_d.active) return;  // the same for the whole cluster
+  const uint32_t Lx = s_d.Lx, Ly = s_d.Ly, W = s_d.W;
+  const uint32_t a = r * Lx / C, b = (r + 1) * Lx / C, nl = b - a;
+  const uint32_t lw = Ly * W;                    // words of one layer
+  const uint32_t pw = (Lx + C - 1) / C * lw;     // words of one local plane
+  uint32_t* s_planes = s_dyn;
+  uint32_t** s_lp = reinterpret_cast<uint32_t**>(s_dyn + 2 * pw);  // 8-byte aligned: 2 pw is even
+  int* s_m = reinterpret_cast<int*>(s_lp + 2 * Lx);
+  const size_t gpl = (size_t)Lx * lw;  // words of one plane in the pool (row stride W)
+  uint32_t* g = pool + s_d.spin_off;
+  for (uint32_t i = threadIdx.x; i < 2 * nl * lw; i += blockDim.x) {
+    const uint32_t X = i >= nl * lw ? 1u : 0u;
+    const uint32_t j = i - X * nl * lw;
+    s_planes[X * pw + j] = ISG_LD(g, X * gpl + (size_t)a * lw + j, 2 * gpl, 77);
+  }
+  for (uint32_t i = threadIdx.x; i < 2 * Lx; i += blockDim.x) {
+    const uint32_t X = i >= Lx ? 1u : 0u, k = i - X * Lx;
+    uint32_t q = 0;
+    while (q + 1 < C && (q + 1) * Lx / C <= k) q++;
+    uint32_t* base = q == r ? s_planes : cl.map_shared_rank(s_planes, q);
+    s_lp[i] = base + X * pw + (k - q * Lx / C) * lw;
+    s_m[i] = 0;
+  }
+  if (threadIdx.x < 4) s_tot[threadIdx.x >> 1][threadIdx.x & 1] = 0;
+  FilmCtx c;
+  c.Lx = Lx; c.Ly = Ly; c.n = s_d.n; c.W = W; c.Wp = W;
+  c.plane_words = lw;
+  c.y_mode = s_d.y_mode; c.x_pbc = s_d.x_pbc; c.rk0 = s_d.rk0; c.rk1 = s_d.rk1;
+  c.last_mask = s_d.last_mask; c.last_calls = s_d.last_calls;
+  c.plane0 = nullptr;
+  c.plane1 = nullptr;
+  c.seam_same = seam_joins_one_colour(Lx, Ly, s_d.y_mode);
+  c.pack = 1;
+  const uint32_t items = nl * (Ly - 1) * W;
+  const SlabRounds rounds = slab_rounds(nl * W, nl * (Ly - 2) * W, blockDim.x);
+  const uint32_t m_every = s_d.measure_every;
+  uint32_t rec_next = s_d.rec_next, nrec = 0, done = 0;
+  // a record's sums are read in the half-sweep after the one that took them
+  // and cleared in the next; two buffers alternate between records
+  int read_buf = -1, clear_buf = -1;
+  uint32_t read_t = 0, read_slot = 0;
+  cl.sync();  // every CTA's planes are in place
+  for (uint32_t k = 0; k < n_sweeps; k++) {
+    const uint32_t t = s_d.sweep + k;
+    if (t >= s_d.sweep_end) break;
+    c.sweep = t;
+    const bool rec_now = m_every != 0 && (t + 1) % m_every == 0;
+    for (uint32_t colour = 0; colour < 2; colour++) {
+      c.colour = colour;
+      if (clear_buf >= 0) {
+        for (uint32_t i = threadIdx.x; i < Lx; i += blockDim.x) s_m[clear_buf * Lx + i] = 0;
+        if (threadIdx.x < 2) s_tot[clear_buf][threadIdx.x] = 0;
+        clear_buf = -1;
+      }
+      if (read_buf >= 0) {
+        cluster_record(cl, s_d, records, s_m, s_tot, (uint32_t)read_buf, a, b, C, read_t, read_slot);
+        clear_buf = read_buf;
+        read_buf = -1;
+      }
+      if (colour == 1 && rec_now) {
+        int* sm = s_m + (nrec & 1u) * Lx;
+        int* st = s_tot[nrec & 1u];
+        uint32_t* stash = s_stash + threadIdx.x * kStashSlots;
+        for (uint32_t j = 0; j < rounds.R; j++) {  // the same count for every thread (warp-wide sums)
+          const uint32_t item = slab_round_item(rounds, threadIdx.x, j, blockDim.x);
+          LayerSums r1, r2;
+          if (item < items) {
+            uint32_t kx, ky, w;
+            slab_item_word(s_d, a, nl, item, kx, ky, w);
+            Fetched f;
+            fetch_word_cl(c, s_lp, kx, ky, w, f);
+            update_fetched_cl<FAST, true>(c, s_lp, f, s_thr, s_alw, stash, &r1, &r2);
+          }
+          add_layer_sums_shared(sm, st, r1);
+          add_layer_sums_shared(sm, st, r2);
+        }
+      } else {
+        for (uint32_t j = 0; j < rounds.R; j++) {
+          const uint32_t item = slab_round_item(rounds, threadIdx.x, j, blockDim.x);
+          if (item >= items) continue;
+          uint32_t kx, ky, w;
+          slab_item_word(s_d, a, nl, item, kx, ky, w);
+          Fetched f;
+          fetch_word_cl(c, s_lp, kx, ky, w, f);
+          update_fetched_cl<FAST, false>(c, s_lp, f, s_thr, s_alw);
+        }
+      }
+      cl.sync();
+    }
+    done = k + 1;
+    if (rec_now) {
+      read_buf = (int)(nrec & 1u);
+      read_t = t + 1;
+      read_slot = s_d.rec_cap ? rec_next % s_d.rec_cap : 0u;
+      rec_next++;
+      nrec++;
+    }
+  }
+  if (read_buf >= 0) cluster_record(cl, s_d, records, s_m, s_tot, (uint32_t)read_buf, a, b, C, read_t, read_slot);
+  for (uint32_t i = threadIdx.x; i < 2 * nl * lw; i += blockDim.x) {
+    const uint32_t X = i >= nl * lw ? 1u : 0u;
+    const uint32_t j = i - X * nl * lw;
+    ISG_ST(g, X * gpl + (size_t)a * lw + j, 2 * gpl, 78, s_planes[X * pw + j]);
+  }
+  if (r == 0 && threadIdx.x == 0) {
+    Fg->sweep = s_d.sweep + done;
+    Fg->rec_next = rec_next;
+  }
+  cl.sync();  // peers may still be reading this CTA's layer sums
+}
+
 // ------------------------------------------------------------- set-up
 
 __global__ void init_kernel(FilmDesc F, uint32_t* __restrict__ pool, int kind, uint32_t flip_lo, int flip_all) {
@@ -1580,6 +1873,103 @@ cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_byt
     return cudaErrorInvalidValue;
   auto* kern = exact ? resident_kernel<false> : resident_kernel<true>;
   return launch_pdl(kern, n_films, threads, smem_bytes, st, films, pool, records, n_sweeps);
+}
+
+uint32_t cluster_smem_bytes(const FilmDesc& d, uint32_t C) {
+  if (C == 0 || C > kClusterMaxSize || d.Lx < C || d.Ly < 2 || d.Wp != d.W) return 0;
+  const uint64_t nlm = (d.Lx + C - 1) / C;
+  const uint64_t bytes = 8ull * nlm * d.Ly * d.W + 24ull * d.Lx;
+  if (bytes > kClusterMaxSmem) return 0;
+  return (uint32_t)bytes;
+}
+
+uint32_t cluster_threads(const FilmDesc& d, uint32_t C, bool exact, uint32_t per_sm) {
+  // a pair item (ky = 1 word and its wrap partner) is two words of work
+  const uint64_t tmax = std::max<uint64_t>(32, cluster_max_threads(exact) / std::max<uint32_t>(per_sm, 1) / 32 * 32);
+  const uint64_t nlm = (d.Lx + C - 1) / C;
+  const uint64_t work = nlm * d.Ly * d.W;
+  const uint64_t rounds = std::max<uint64_t>(1, (work + tmax - 1) / tmax);
+  const uint64_t t = ((work + rounds - 1) / rounds + 31) / 32 * 32;
+  return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(t, 32), tmax);
+}
+
+namespace {
+
+// Dynamic shared memory of a launch with per_sm CTAs per SM: at least what the
+// films need, and enough that per_sm + 1 CTAs (with the kernel's static
+// shared memory and the per-block reserve) do not fit in one SM.
+template <typename K>
+cudaError_t cluster_launch_smem(K kern, uint32_t needed, uint32_t per_sm, uint32_t* out) {
+  int dev = 0, per_smp = 0, reserve = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_smp, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const uint64_t fixed = (uint64_t)fa.sharedSizeBytes + (uint64_t)reserve;
+  uint64_t pad = (uint64_t)per_smp / (per_sm + 1) + 1;  // per_sm + 1 CTAs of this size overflow the SM
+  pad = pad > fixed ? (pad - fixed + 127) / 128 * 128 : 0;
+  uint64_t smem = std::max<uint64_t>(needed, pad);
+  if (smem > kClusterMaxSmem) smem = std::max<uint64_t>(needed, kClusterMaxSmem);
+  *out = (uint32_t)smem;
+  return cudaSuccess;
+}
+
+template <typename K>
+cudaLaunchConfig_t cluster_config(K kern, uint32_t grid, uint32_t C, uint32_t smem, uint32_t threads,
+                                  cudaStream_t st, cudaLaunchAttribute* attr, cudaError_t* e) {
+  *e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterMaxSmem);
+  // the whole unified L1 as shared memory, so that per_sm padded CTAs fit
+  if (*e == cudaSuccess)
+    *e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+}  // namespace
+
+int cluster_capacity(uint32_t C, uint32_t per_sm, uint32_t smem_bytes, uint32_t threads, bool exact) {
+  if (C == 0 || C > kClusterMaxSize || per_sm == 0 || per_sm > kClusterMaxPerSm || smem_bytes > kClusterMaxSmem ||
+      threads == 0 || threads > cluster_max_threads(exact) || threads % 32u)
+    return 0;
+  auto* kern = exact ? cluster_kernel<false> : cluster_kernel<true>;
+  uint32_t smem = 0;
+  if (cluster_launch_smem(kern, smem_bytes, per_sm, &smem) != cudaSuccess) return -1;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e;
+  cudaLaunchConfig_t cfg = cluster_config(kern, C, C, smem, threads, nullptr, attr, &e);
+  if (e != cudaSuccess) return -1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) return -1;
+  return n;
+}
+
+cudaError_t launch_cluster(FilmDesc* films, uint32_t n_films, uint32_t C, uint32_t per_sm, uint32_t smem_bytes,
+                           uint32_t threads, bool exact, uint32_t* pool, int64_t* records, uint32_t n_sweeps,
+                           cudaStream_t st) {
+  if (n_films == 0 || n_sweeps == 0) return cudaSuccess;
+  if (C == 0 || C > kClusterMaxSize || per_sm == 0 || per_sm > kClusterMaxPerSm || smem_bytes > kClusterMaxSmem ||
+      threads == 0 || threads > cluster_max_threads(exact) || threads % 32u)
+    return cudaErrorInvalidValue;
+  auto* kern = exact ? cluster_kernel<false> : cluster_kernel<true>;
+  uint32_t smem = 0;
+  cudaError_t e = cluster_launch_smem(kern, smem_bytes, per_sm, &smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config(kern, n_films * C, C, smem, threads, st, attr, &e);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&cfg, kern, films, pool, records, n_sweeps);
 }
 
 int read_oob_counters(unsigned long long* count, unsigned long long* first) {

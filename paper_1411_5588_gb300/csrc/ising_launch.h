@@ -64,6 +64,21 @@ constexpr uint64_t kResidentMaxSites = 1ull << 16;
 constexpr uint64_t kResidentAutoSites = 1ull << 15;
 constexpr uint32_t kResidentMaxSmem = 48u * 1024u;
 
+// Cluster-resident path: a thread-block cluster of C CTAs (C <= kClusterMaxSize)
+// holds one film in distributed shared memory for a whole call of sweeps,
+// each CTA a slab of ceil(Lx / C) layers or one fewer.  kClusterThreads is the
+// most threads a CTA runs (one CTA per SM at the update body's registers);
+// kClusterMaxSmem the most dynamic shared memory a CTA takes.  The exact-table
+// variant (a strict compare and a mux tree per site) needs more registers, so
+// it runs at most kClusterThreadsExact.
+constexpr uint32_t kClusterThreads = 768;
+constexpr uint32_t kClusterThreadsExact = 512;
+__host__ __device__ constexpr uint32_t cluster_max_threads(bool exact) {
+  return exact ? kClusterThreadsExact : kClusterThreads;
+}
+constexpr uint32_t kClusterMaxSize = 8;
+constexpr uint32_t kClusterMaxSmem = 200u * 1024u;
+
 // Device arrays describing the films of a launch.
 struct LaunchSet {
   FilmDesc* films = nullptr;         // n_films descriptors
@@ -110,6 +125,31 @@ uint32_t resident_threads(const FilmDesc& d);
 // the largest.  The kernel advances each descriptor's sweep and rec_next.
 cudaError_t launch_resident(FilmDesc* films, uint32_t n_films, uint32_t smem_bytes, uint32_t threads, bool exact,
                             uint32_t* pool, int64_t* records, uint32_t n_sweeps, cudaStream_t st);
+// Dynamic shared memory of a CTA of film d on the cluster-resident path with
+// clusters of C CTAs, 0 if the film does not qualify (C out of range, fewer
+// layers than C, or too large).
+uint32_t cluster_smem_bytes(const FilmDesc& d, uint32_t C);
+// CTAs of the cluster path that share one SM (1..kClusterMaxPerSm): a CTA's
+// half-sweep ends at a cluster barrier where its warps wait for the slowest,
+// and CTAs of other films on the same SM fill that wait.  per_sm divides the
+// threads a CTA may run, and the launch pads each CTA's shared memory so
+// that no more than per_sm CTAs fit on an SM.
+constexpr uint32_t kClusterMaxPerSm = 3;
+// Threads per CTA for film d with clusters of C CTAs, per_sm CTAs per SM: the
+// slab's update items spread over as few full rounds as
+// cluster_max_threads(exact) / per_sm allows (a multiple of 32).
+uint32_t cluster_threads(const FilmDesc& d, uint32_t C, bool exact, uint32_t per_sm);
+// Clusters of C CTAs (smem_bytes of dynamic shared memory needed and threads
+// each, per_sm of them per SM) that one GPU can hold at once (0: such a
+// launch cannot run), or -1 on a CUDA error.
+int cluster_capacity(uint32_t C, uint32_t per_sm, uint32_t smem_bytes, uint32_t threads, bool exact);
+// n_sweeps sweeps (with their records) of films[0..n_films) on the cluster
+// path, one cluster of C CTAs per film, per_sm CTAs per SM; every film must
+// qualify for C, and smem_bytes and threads cover the largest.  The kernel
+// advances each descriptor's sweep and rec_next.
+cudaError_t launch_cluster(FilmDesc* films, uint32_t n_films, uint32_t C, uint32_t per_sm, uint32_t smem_bytes,
+                           uint32_t threads, bool exact, uint32_t* pool, int64_t* records, uint32_t n_sweeps,
+                           cudaStream_t st);
 // Checked builds: the out-of-range access counters (returns 1); other
 // builds return 0 with both zero; -1 on a CUDA error.
 int read_oob_counters(unsigned long long* count, unsigned long long* first);

@@ -1,6 +1,6 @@
 """The library built with ISING_CHECKED (every lattice word index of the
-update, resident and record kernels and of the allocation-free measurement
-tested against its plane): all parity
+update, resident, cluster and record kernels and of the allocation-free
+measurement tested against its plane): all parity
 shapes and a set of random films, every launch shape, bit-identical to the
 oracle, and not one out-of-range access.  Runs in a child process, because a
 process loads one build of the library."""
@@ -42,6 +42,20 @@ for shape in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q):
     b.set_shape(shape)
     b.sweep(4, False)
 b.close()
+# the cluster-resident path: one CTA per film, then three (films of three
+# layers or more), against the oracle
+for C, sub in ((1, specs), (3, [f for f in specs if f["Lx"] >= 3])):
+    sub = [dict(f, measure_every=1 + i % 2) for i, f in enumerate(sub)]
+    b = ig.Batch(sub, lanes=1)
+    b.set_cluster_size(C)
+    b.set_shape(ig.SHAPE_CLUSTER)
+    b.sweep(5, False)
+    for i, f in enumerate(sub):
+        o = R._oracle(f)
+        assert np.array_equal(b.read_series(i), o.sweep(5, f["measure_every"])), (C, f)
+        assert np.array_equal(b.get_spins(i), o.get_spins()), (C, f)
+        films += 1
+    b.close()
 # the allocation-free measurement (its own kernel, the same record code)
 import ctypes
 import torch
