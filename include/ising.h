@@ -83,13 +83,16 @@ enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
  * GRID_Q    the same with four threads per word, each drawing two of its
  *           eight Philox calls: four times the threads for the same work,
  *           for films too small to fill the GPU otherwise.
- * CLUSTER   (batches only) one thread-block cluster of C CTAs per film
- *           keeps the film in distributed shared memory for a whole
+ * CLUSTER   (batches only) a thread-block cluster of C CTAs keeps a film in
+ *           distributed shared memory for all sweeps of an
  *           ising_batch_sweep call, CTA r holding layers [r Lx / C,
- *           (r+1) Lx / C) of both parity planes; a cluster barrier separates
- *           the half-sweeps, so films never wait for one another and no
- *           launch boundary falls between half-sweeps (the Appendix's many
- *           independent films, each on its own few SMs).
+ *           (r+1) Lx / C) of both parity planes, a cluster barrier between
+ *           half-sweeps; then it takes its next film.  Each lane runs
+ *           n_SM / (C lanes) clusters, one CTA per SM, and its films go to
+ *           them largest first, each to the cluster with the least work so
+ *           far.  Films never wait for one another and no launch boundary
+ *           falls between half-sweeps (the Appendix's many independent
+ *           films, each on its own few SMs).
  * AUTO      the autotuner's measurement for this film shape and record
  *           interval if there is one, else RESIDENT up to 32768 spins and
  *           GRID_1 above. */
@@ -279,7 +282,7 @@ int ising_batch_set_cluster_size(ising_batch *b, uint32_t cluster_size);
 int ising_batch_get_cluster_size(const ising_batch *b, uint32_t *cluster_size);
 
 /* Autotuner: times GRID_1, GRID_2, GRID_Q and CLUSTER at every cluster size
- * for which all films qualify and their clusters fit on the GPU at once, on a
+ * for which all films qualify, on a
  * scratch batch of the same jobs in the same lanes (from their initial
  * states; the kernels' work does not depend on the spins), all lanes
  * running, graph replay and records included, and adopts the fastest for

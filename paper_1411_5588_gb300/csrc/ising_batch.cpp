@@ -37,6 +37,8 @@ struct Lane {
   // launch's shared memory and threads per CTA and its table variant
   uint32_t cl_size = 0, cl_per_sm = 1, cl_smem = 0, cl_threads = 0;
   bool cl_exact = false;
+  uint32_t cl_clusters = 0;        // clusters of the lane's launch
+  uint32_t* d_cl_list = nullptr;   // their film lists (launch_cluster's list)
 
   void drop_graphs() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
@@ -143,18 +145,62 @@ int lane_cluster_params(const Lane* b, uint32_t C, uint32_t per_sm, uint32_t* sm
   return ISING_OK;
 }
 
-// Switch the lane to the cluster path with C CTAs per film, per_sm per SM
-// (C = 0: back to the grid kernels).
-int lane_apply_cluster(Lane* b, uint32_t C, uint32_t per_sm) {
+// Work of one sweep of film d in units of about one Philox call: a row's
+// words' calls plus a few per word for the fetch and the neighbour count.
+double cluster_film_work(const FilmDesc& d) {
+  return (double)d.Lx * d.Ly * (8.0 * (d.W - 1) + d.last_calls + 3.0 * d.W);
+}
+
+// Switch the lane to the cluster path with C CTAs per film (C = 0: back to
+// the grid kernels), on n_clusters clusters of one CTA per SM: the films go
+// to clusters largest first, each to the cluster with the least work so far.
+int lane_apply_cluster(Lane* b, uint32_t C, uint32_t n_clusters) {
+  const uint32_t per_sm = 1;
   uint32_t smem = 0, threads = 0;
   bool exact = false;
+  const size_t nf = b->fs.h.size();
   if (C) {
     int rc = lane_cluster_params(b, C, per_sm, &smem, &threads, &exact);
     if (rc) return rc;
+    n_clusters = (uint32_t)std::min<size_t>(std::max<uint32_t>(n_clusters, 1), nf);
   }
-  if (b->cl_size == C && (C == 0 || b->cl_per_sm == per_sm)) return ISING_OK;
+  if (b->cl_size == C && (C == 0 || b->cl_clusters == n_clusters)) return ISING_OK;
+  std::vector<uint32_t> list;
+  if (C) {
+    std::vector<size_t> order(nf);
+    std::iota(order.begin(), order.end(), (size_t)0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+      return cluster_film_work(b->fs.h[x]) > cluster_film_work(b->fs.h[y]);
+    });
+    std::vector<double> load(n_clusters, 0.0);
+    std::vector<std::vector<uint32_t>> members(n_clusters);
+    for (size_t f : order) {
+      const size_t c = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+      members[c].push_back((uint32_t)f);
+      load[c] += cluster_film_work(b->fs.h[f]);
+    }
+    list.resize(n_clusters + 1 + nf);
+    uint32_t o = 0;
+    for (uint32_t c = 0; c < n_clusters; c++) {
+      list[c] = o;
+      for (uint32_t f : members[c]) list[n_clusters + 1 + o++] = f;
+    }
+    list[n_clusters] = o;
+  }
   ISG_CK(cudaStreamSynchronize(b->fs.stream));
+  if (b->d_cl_list) {
+    cudaFree(b->d_cl_list);
+    b->d_cl_list = nullptr;
+  }
+  if (C) {
+    if (dev_alloc(&b->d_cl_list, list.size() * sizeof(uint32_t)) != cudaSuccess) {
+      b->cl_size = 0;
+      return fail(ISING_ENOMEM, "cannot allocate the cluster film lists");
+    }
+    ISG_CK(cudaMemcpy(b->d_cl_list, list.data(), list.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  }
   b->cl_size = C;
+  b->cl_clusters = C ? n_clusters : 0;
   b->cl_per_sm = per_sm;
   b->cl_smem = smem;
   b->cl_threads = threads;
@@ -169,8 +215,8 @@ int lane_cluster_sweeps(Lane* b, uint64_t n) {
   FilmSet& fs = b->fs;
   while (n) {
     const uint32_t k = (uint32_t)std::min<uint64_t>(n, 4096);
-    ISG_CK(launch_cluster(fs.L.films, (uint32_t)fs.h.size(), b->cl_size, b->cl_per_sm, b->cl_smem, b->cl_threads,
-                          b->cl_exact, fs.pool, fs.rec, k, fs.stream));
+    ISG_CK(launch_cluster(fs.L.films, b->d_cl_list, b->cl_clusters, b->cl_size, b->cl_per_sm, b->cl_smem,
+                          b->cl_threads, b->cl_exact, fs.pool, fs.rec, k, fs.stream));
     for (auto& d : fs.h) d.sweep += k;
     b->sweeps += k;
     n -= k;
@@ -262,6 +308,7 @@ void lane_destroy(Lane* b) {
   if (b->fs.stream) cudaStreamSynchronize(b->fs.stream);
   b->drop_graphs();
   if (b->d_stage) cudaFree(b->d_stage);
+  if (b->d_cl_list) cudaFree(b->d_cl_list);
   if (b->ev_done) cudaEventDestroy(b->ev_done);
   b->fs.release();
   delete b;
@@ -366,29 +413,24 @@ namespace {
 
 int batch_apply_items(ising_batch* b, uint32_t items) {
   for (Lane* l : b->lanes) {
-    int rc = lane_apply_cluster(l, 0, 1);
+    int rc = lane_apply_cluster(l, 0, 0);
     if (!rc) rc = lane_apply_items(l, items);
     if (rc) return rc;
   }
   return ISING_OK;
 }
 
-// CTAs per SM of the cluster path with C CTAs per film: as many as the
-// batch's n C CTAs need to be resident at once, at most kClusterMaxPerSm.
-uint32_t batch_cluster_per_sm(const ising_batch* b, uint32_t C) {
-  const uint64_t n_sm = (uint64_t)std::max(1, b->lanes[0]->fs.n_sm);
-  const uint64_t k = ((uint64_t)b->jobs.size() * C + n_sm - 1) / n_sm;
-  return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(k, 1), kClusterMaxPerSm);
-}
-
-// Every lane on the cluster path with C CTAs per film; on EINVAL (some film
-// does not qualify) every lane is back on the grid kernels.
+// Every lane on the cluster path with C CTAs per film, the GPU's SMs shared
+// out among the lanes (one CTA each, so a lane has n_SM / (C lanes) clusters,
+// at least one); on EINVAL (some film does not qualify) every lane is back on
+// the grid kernels.
 int batch_apply_cluster(ising_batch* b, uint32_t C) {
-  const uint32_t per_sm = batch_cluster_per_sm(b, C);
+  const uint32_t n_sm = (uint32_t)std::max(1, b->lanes[0]->fs.n_sm);
+  const uint32_t per_lane = std::max<uint32_t>(1, n_sm / (C * (uint32_t)b->lanes.size()));
   for (Lane* l : b->lanes) {
-    int rc = lane_apply_cluster(l, C, per_sm);
+    int rc = lane_apply_cluster(l, C, per_lane);
     if (rc) {
-      for (Lane* m : b->lanes) lane_apply_cluster(m, 0, 1);
+      for (Lane* m : b->lanes) lane_apply_cluster(m, 0, 0);
       return rc;
     }
   }
@@ -596,24 +638,32 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   if (rc) return rc;
   double sites = 0;
   for (const auto& j : b->jobs) sites += (double)j.Lx * j.Ly * j.Lz;
-  const uint64_t n = (uint64_t)std::min(1024.0, std::max(64.0, std::round(4e8 / sites)));
+  uint64_t n = (uint64_t)std::min(1024.0, std::max(64.0, std::round(4e8 / sites)));
+  // the grid shapes replay captured chunks only in calls of two chunks or
+  // more (lane_sweep), as long runs do: where launch overhead matters (small
+  // sets), time calls that long
+  uint64_t G = 1;
+  for (const auto& j : b->jobs)
+    if (j.measure_every) G = lcm_u64(G, j.measure_every);
+  if (G == 1) G = 64;
+  while (G < 16) G *= 2;
+  if (G <= 4096 && sites * 2.0 * (double)G <= 4e10) n = std::max<uint64_t>(n, 2 * G);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(ISING_ECUDA, "event creation failed");
   int best = ISING_SHAPE_GRID_1;
   uint32_t best_cl = 0;
   float best_ms = 3.0e38f;
-  // grid shapes, then the cluster path at each cluster size whose clusters
-  // all fit on the GPU at once (or 1 CTA per film when the films outnumber
-  // the SMs) and for which every film qualifies
+  // grid shapes, then the cluster path at each cluster size for which every
+  // film qualifies
   std::vector<std::pair<int, uint32_t>> cands = {
       {ISING_SHAPE_GRID_1, 0}, {ISING_SHAPE_GRID_2, 0}, {ISING_SHAPE_GRID_Q, 0}};
   {
     const size_t nf = b->jobs.size();
     const size_t n_sm = (size_t)std::max(1, b->lanes[0]->fs.n_sm);
-    for (uint32_t C = 1; C <= kClusterMaxSize; C++) {
-      if (C > 1 && nf * C > kClusterMaxPerSm * n_sm) break;
-      const uint32_t per_sm = batch_cluster_per_sm(b, C);
+    (void)nf;
+    for (uint32_t C = 1; C <= kClusterMaxSize && C * b->lanes.size() <= n_sm; C++) {
+      const uint32_t per_sm = 1;
       bool ok = true;
       for (const Lane* l : b->lanes) {
         uint32_t smem = 0, threads = 0;

@@ -1534,25 +1534,19 @@ __device__ __forceinline__ void cluster_record(cg::cluster_group& cl, const Film
   }
 }
 
-// n_sweeps sweeps of film blockIdx.x / C (C = the cluster's size), records
-// into its ring, sweep and rec_next advanced at the end.  Dynamic shared
-// memory: planes [2][ceil(Lx / C)][Ly][W] words, the layer table (2 Lx
-// generic addresses), and two buffers of Lx layer sums.
+// n_sweeps sweeps of film Fg on this cluster (C = its size), records into
+// its ring, sweep and rec_next advanced at the end.  Dynamic shared memory
+// s_dyn: planes [2][ceil(Lx / C)][Ly][W] words, the layer table (2 Lx
+// generic addresses), and two buffers of Lx layer sums.  Ends with a cluster
+// barrier, after which the CTA's shared memory is free for the next film.
 template <bool FAST>
-__global__ void __launch_bounds__(cluster_max_threads(!FAST), 1)
-cluster_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64_t* __restrict__ records,
-               uint32_t n_sweeps) {
-  extern __shared__ __align__(16) uint32_t s_dyn[];
+__device__ __forceinline__ void cluster_film(cg::cluster_group& cl, FilmDesc* Fg, uint32_t* __restrict__ pool,
+                                             int64_t* __restrict__ records, uint32_t n_sweeps, FilmDesc& s_d,
+                                             uint32_t* s_thr, uint32_t* s_alw, uint32_t* s_stash, int (*s_tot)[2],
+                                             uint32_t* s_dyn) {
   constexpr uint32_t kDescWords = sizeof(FilmDesc) / 4;
-  __shared__ __align__(16) FilmDesc s_d;
-  __shared__ __align__(16) uint32_t s_thr[64];
-  __shared__ __align__(16) uint32_t s_alw[64];
-  __shared__ uint32_t s_stash[kStashSlots * kClusterThreads];
-  __shared__ int s_tot[2][2];  // {B, M} of the record being summed, two buffers
-  cg::cluster_group cl = cg::this_cluster();
   const uint32_t C = cl.num_blocks();
   const uint32_t r = cl.block_rank();
-  FilmDesc* Fg = films + blockIdx.x / C;
   {
     const uint4* src = reinterpret_cast<const uint4*>(Fg);
     uint4* dst = reinterpret_cast<uint4*>(&s_d);
@@ -1673,6 +1667,31 @@ cluster_kernel(FilmDesc* __restrict__ films, uint32_t* __restrict__ pool, int64_
     Fg->rec_next = rec_next;
   }
   cl.sync();  // peers may still be reading this CTA's layer sums
+}
+
+// Clusters of C CTAs, cluster i sweeping films list[n_clusters + 1 + j] for j
+// in [list[i], list[i + 1]) one after another (all n_sweeps sweeps of one,
+// then the next): films never wait for one another, and the host packs them
+// so that the clusters' loads are about equal.
+template <bool FAST>
+__global__ void __launch_bounds__(cluster_max_threads(!FAST), 1)
+cluster_kernel(FilmDesc* __restrict__ films, const uint32_t* __restrict__ list, uint32_t n_clusters,
+               uint32_t* __restrict__ pool, int64_t* __restrict__ records, uint32_t n_sweeps) {
+  extern __shared__ __align__(16) uint32_t s_dyn[];
+  __shared__ __align__(16) FilmDesc s_d;
+  __shared__ __align__(16) uint32_t s_thr[64];
+  __shared__ __align__(16) uint32_t s_alw[64];
+  __shared__ uint32_t s_stash[kStashSlots * kClusterThreads];
+  __shared__ int s_tot[2][2];  // {B, M} of the record being summed, two buffers
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t ci = blockIdx.x / cl.num_blocks();
+  if (ci >= n_clusters) return;  // the same for the whole cluster
+  const uint32_t j1 = list[ci + 1];
+  for (uint32_t j = list[ci]; j < j1; j++) {
+    __syncthreads();  // every thread is done with the previous film's descriptor
+    cluster_film<FAST>(cl, films + list[n_clusters + 1 + j], pool, records, n_sweeps, s_d, s_thr, s_alw, s_stash,
+                       s_tot, s_dyn);
+  }
 }
 
 // ------------------------------------------------------------- set-up
@@ -1955,10 +1974,10 @@ int cluster_capacity(uint32_t C, uint32_t per_sm, uint32_t smem_bytes, uint32_t 
   return n;
 }
 
-cudaError_t launch_cluster(FilmDesc* films, uint32_t n_films, uint32_t C, uint32_t per_sm, uint32_t smem_bytes,
-                           uint32_t threads, bool exact, uint32_t* pool, int64_t* records, uint32_t n_sweeps,
-                           cudaStream_t st) {
-  if (n_films == 0 || n_sweeps == 0) return cudaSuccess;
+cudaError_t launch_cluster(FilmDesc* films, const uint32_t* list, uint32_t n_clusters, uint32_t C, uint32_t per_sm,
+                           uint32_t smem_bytes, uint32_t threads, bool exact, uint32_t* pool, int64_t* records,
+                           uint32_t n_sweeps, cudaStream_t st) {
+  if (n_clusters == 0 || n_sweeps == 0) return cudaSuccess;
   if (C == 0 || C > kClusterMaxSize || per_sm == 0 || per_sm > kClusterMaxPerSm || smem_bytes > kClusterMaxSmem ||
       threads == 0 || threads > cluster_max_threads(exact) || threads % 32u)
     return cudaErrorInvalidValue;
@@ -1967,9 +1986,9 @@ cudaError_t launch_cluster(FilmDesc* films, uint32_t n_films, uint32_t C, uint32
   cudaError_t e = cluster_launch_smem(kern, smem_bytes, per_sm, &smem);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = cluster_config(kern, n_films * C, C, smem, threads, st, attr, &e);
+  cudaLaunchConfig_t cfg = cluster_config(kern, n_clusters * C, C, smem, threads, st, attr, &e);
   if (e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, kern, films, pool, records, n_sweeps);
+  return cudaLaunchKernelEx(&cfg, kern, films, list, n_clusters, pool, records, n_sweeps);
 }
 
 int read_oob_counters(unsigned long long* count, unsigned long long* first) {

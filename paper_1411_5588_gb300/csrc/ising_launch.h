@@ -71,7 +71,7 @@ constexpr uint32_t kResidentMaxSmem = 48u * 1024u;
 // kClusterMaxSmem the most dynamic shared memory a CTA takes.  The exact-table
 // variant (a strict compare and a mux tree per site) needs more registers, so
 // it runs at most kClusterThreadsExact.
-constexpr uint32_t kClusterThreads = 768;
+constexpr uint32_t kClusterThreads = 704;
 constexpr uint32_t kClusterThreadsExact = 512;
 __host__ __device__ constexpr uint32_t cluster_max_threads(bool exact) {
   return exact ? kClusterThreadsExact : kClusterThreads;
@@ -143,13 +143,15 @@ uint32_t cluster_threads(const FilmDesc& d, uint32_t C, bool exact, uint32_t per
 // each, per_sm of them per SM) that one GPU can hold at once (0: such a
 // launch cannot run), or -1 on a CUDA error.
 int cluster_capacity(uint32_t C, uint32_t per_sm, uint32_t smem_bytes, uint32_t threads, bool exact);
-// n_sweeps sweeps (with their records) of films[0..n_films) on the cluster
-// path, one cluster of C CTAs per film, per_sm CTAs per SM; every film must
-// qualify for C, and smem_bytes and threads cover the largest.  The kernel
-// advances each descriptor's sweep and rec_next.
-cudaError_t launch_cluster(FilmDesc* films, uint32_t n_films, uint32_t C, uint32_t per_sm, uint32_t smem_bytes,
-                           uint32_t threads, bool exact, uint32_t* pool, int64_t* records, uint32_t n_sweeps,
-                           cudaStream_t st);
+// n_sweeps sweeps (with their records) of films on the cluster path:
+// n_clusters clusters of C CTAs, per_sm CTAs per SM, cluster i sweeping the
+// films list[n_clusters + 1 + j], j in [list[i], list[i + 1]), one after
+// another (list: device memory).  Every listed film must qualify for C, and
+// smem_bytes and threads cover the largest.  The kernel advances each
+// descriptor's sweep and rec_next.
+cudaError_t launch_cluster(FilmDesc* films, const uint32_t* list, uint32_t n_clusters, uint32_t C, uint32_t per_sm,
+                           uint32_t smem_bytes, uint32_t threads, bool exact, uint32_t* pool, int64_t* records,
+                           uint32_t n_sweeps, cudaStream_t st);
 // Checked builds: the out-of-range access counters (returns 1); other
 // builds return 0 with both zero; -1 on a CUDA error.
 int read_oob_counters(unsigned long long* count, unsigned long long* first);

@@ -1,8 +1,9 @@
 """The cluster-resident path (ISING_SHAPE_CLUSTER) against the CPU oracle, bit
 for bit.
 
-One thread-block cluster of C CTAs keeps each film of a batch in distributed
-shared memory for a whole call, CTA r holding a slab of layers; a word's
+A thread-block cluster of C CTAs keeps a film of a batch in distributed
+shared memory for a whole call, CTA r holding a slab of layers, then takes
+its next film; a word's
 x-neighbour across a slab boundary, and the mirrored layer of an Eq. 11
 partner row, come from a peer CTA.  So the cases cover every cluster size
 with slabs of one layer and of several, uneven slabs (Lx not a multiple of
@@ -151,6 +152,24 @@ def test_cluster_and_grid_shapes_alternate(seed):
         w = np.concatenate(want[i])
         assert np.array_equal(g, w), (seed, i, sp)
         assert np.array_equal(b.get_spins(i), oracles[i].get_spins()), (seed, i, sp)
+    b.close()
+
+
+@pytest.mark.parametrize("C", [1, 4, 8])
+def test_clusters_take_several_films_in_turn(C):
+    """Sixteen lanes: each lane gets n_SM / (C x 16) clusters (one for C = 8
+    on 152 SMs), fewer than its films, so a cluster sweeps two or more films
+    one after another, every sweep of the call for each, records included;
+    films of every size share a cluster (largest-first packing)."""
+    films = [f for f in FILMS if f[0] >= C]
+    specs = [_spec(films[i % len(films)], i, 1 + i % 3) for i in range(40)]
+    b = ig.Batch(specs, lanes=16)
+    b.set_cluster_size(C)
+    b.set_shape(ig.SHAPE_CLUSTER)
+    calls = [(2, False), (9, True)]
+    for n, g in calls:
+        b.sweep(n, g)
+    _check(b, specs, calls)
     b.close()
 
 

@@ -414,7 +414,7 @@ def test_batch_autotune_leaves_the_chains_alone():
     b = ig.Batch(specs)
     b.sweep(4, True)
     best = b.autotune()
-    assert best in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q) and b.get_shape() == best
+    assert best in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q, ig.SHAPE_CLUSTER) and b.get_shape() == best
     b.sweep(40, True)
     for i, sp in enumerate(specs):
         o = O.Film(sp["Lx"], sp["Ly"], sp["Lz"], 1.0, sp["H1"], sp["T"], sp["seed"], replica=sp["replica"])
