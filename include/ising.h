@@ -276,8 +276,10 @@ int ising_batch_set_shape(ising_batch *b, int shape);
 int ising_batch_get_shape(ising_batch *b, int *shape);
 /* CTAs per film of the CLUSTER shape: 1..8, or 0 for the automatic choice
  * above.  EINVAL if > 8 or some film does not qualify (nothing changes).
- * Takes effect at once when the batch is on CLUSTER.  get: the size the
- * batch runs with now, 0 when it is on a grid shape. */
+ * Takes effect at once when the batch runs on the cluster path (CLUSTER
+ * set, or AUTO after the autotuner chose it; 0 then restores the automatic
+ * or the autotuner's size).  get: the size the batch runs with now, 0 when
+ * it is on a grid shape. */
 int ising_batch_set_cluster_size(ising_batch *b, uint32_t cluster_size);
 int ising_batch_get_cluster_size(const ising_batch *b, uint32_t *cluster_size);
 

@@ -614,8 +614,10 @@ int ising_batch_set_cluster_size(ising_batch* b, uint32_t cluster_size) {
     }
   }
   b->cl_pinned = cluster_size;
-  if (b->lanes[0]->cl_size && b->shape == ISING_SHAPE_CLUSTER)
-    return batch_apply_cluster(b, cluster_size ? cluster_size : batch_auto_cluster(b));
+  if (b->lanes[0]->cl_size)  // on the cluster path now (pinned, or the autotuner's pick)
+    return batch_apply_cluster(b, cluster_size ? cluster_size
+                                               : (b->shape == ISING_SHAPE_CLUSTER ? batch_auto_cluster(b)
+                                                                                  : b->tuned_cl));
   return ISING_OK;
 }
 

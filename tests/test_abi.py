@@ -116,3 +116,15 @@ def test_batch_jobs_are_checked_before_any_device_call():
     with pytest.raises(ig.IsingError) as e:
         ig.Batch([])
     assert e.value.status == ig.EINVAL
+
+
+def test_cluster_size_calls_reject_null_handles():
+    """The cluster-shape calls check their arguments before touching a batch
+    (no device needed)."""
+    import paper_1411_5588_gb300 as ig
+    L = ig.lib()
+    v = ctypes.c_uint32(7)
+    assert L.ising_batch_set_cluster_size(None, 2) == ig.EINVAL
+    assert L.ising_batch_get_cluster_size(None, ctypes.byref(v)) == ig.EINVAL
+    assert v.value == 7
+    assert ig.SHAPE_CLUSTER == 5

@@ -212,12 +212,26 @@ def test_cluster_size_limits():
     b.close()
 
 
-def test_autotune_with_cluster_candidates_leaves_the_chains_alone():
-    specs = [_spec(f, i, 1) for i, f in enumerate(FILMS)]
+@pytest.mark.parametrize("small", [False, True], ids=["mixed-films", "two-small-films"])
+def test_autotune_with_cluster_candidates_leaves_the_chains_alone(small):
+    """The autotuner may pick the cluster path (two small films, where a
+    grid half-sweep is mostly launch overhead, usually take it); a size
+    pinned afterwards applies at once, and 0 restores the autotuner's."""
+    films = FILMS[:2] if small else FILMS
+    specs = [_spec(f, i, 1) for i, f in enumerate(films)]
     b = ig.Batch(specs)
     shape = b.autotune()
     assert shape in (ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q, ig.SHAPE_CLUSTER)
     assert b.get_shape() == shape
+    calls = [(17, True)]
     b.sweep(17, True)
-    _check(b, specs, [(17, True)])
+    if shape == ig.SHAPE_CLUSTER:
+        tuned = b.cluster_size
+        b.set_cluster_size(1)
+        assert b.cluster_size == 1
+        b.sweep(5, False)
+        b.set_cluster_size(0)
+        assert b.cluster_size == tuned
+        calls.append((5, False))
+    _check(b, specs, calls)
     b.close()
