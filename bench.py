@@ -39,7 +39,7 @@ def alu_frac(attempts_per_ns):
 
 SHAPE_NAMES = {0: "auto", 1: "resident", 2: "grid, 1 word/thread", 3: "grid, 2 words/thread",
                4: "grid, 4 threads/word", 5: "cluster-resident"}
-SHAPE_FLAGS = {1: "resident", 2: "grid1", 3: "grid2", 4: "gridq"}
+SHAPE_FLAGS = {1: "resident", 2: "grid1", 3: "grid2", 4: "gridq", 5: "cluster"}
 METRIC = "spin-flip attempts/ns on 1 GB300, batched vs plain, % roofline; p99 latency"
 UNIT = "attempts/ns"
 SWEEPS_PER_STEP = 10

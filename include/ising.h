@@ -83,11 +83,13 @@ enum { ISING_INIT_RANDOM = 0, ISING_INIT_SLAB_Y = 1, ISING_INIT_ALL_UP = 2 };
  * GRID_Q    the same with four threads per word, each drawing two of its
  *           eight Philox calls: four times the threads for the same work,
  *           for films too small to fill the GPU otherwise.
- * CLUSTER   (batches only) a thread-block cluster of C CTAs keeps a film in
- *           distributed shared memory for all sweeps of an
+ * CLUSTER   a thread-block cluster of C CTAs keeps a film in distributed
+ *           shared memory for all sweeps of an ising_sweep or
  *           ising_batch_sweep call, CTA r holding layers [r Lx / C,
  *           (r+1) Lx / C) of both parity planes, a cluster barrier between
- *           half-sweeps; then it takes its next film.  Each lane runs
+ *           half-sweeps; then it takes its next film.  A single film runs on
+ *           one cluster of the largest C <= 8 it qualifies for (see
+ *           ising_batch_set_shape).  In a batch each lane runs
  *           n_SM / (C lanes) clusters, one CTA per SM, and its films go to
  *           them largest first, each to the cluster with the least work so
  *           far.  Films never wait for one another and no launch boundary
@@ -158,7 +160,8 @@ int ising_set_sweep(ising *h, uint64_t sweep);
 int ising_reserve_records(ising *h, uint64_t n_records);
 
 /* Pin the launch shape of this handle's ising_sweep calls (ISING_SHAPE_*;
- * AUTO unpins).  RESIDENT on a film that does not qualify is EINVAL. */
+ * AUTO unpins).  RESIDENT or CLUSTER on a film that does not qualify is
+ * EINVAL. */
 int ising_set_shape(ising *h, int shape);
 
 /* The shape an ising_sweep(h, n, measure_every) call would use now. */
@@ -170,7 +173,7 @@ int ising_get_shape(ising *h, uint32_t measure_every, int *shape);
  * fastest goes into a process-wide table keyed by (Lx, Ly, Lz, boundary
  * modes, table variant, record interval up to 16) that every AUTO handle of
  * that key then uses; *shape (may be NULL) receives it.  Shapes are tried
- * in the order RESIDENT, GRID_1, GRID_2, GRID_Q, and a later one must be at least 2%
+ * in the order RESIDENT, GRID_1, GRID_2, GRID_Q, CLUSTER, and a later one must be at least 2%
  * faster to win.  Synchronises. */
 int ising_autotune(ising *h, uint32_t measure_every, int *shape);
 

@@ -279,6 +279,7 @@ struct ising {
   int8_t* d_stage = nullptr;
   bool dirty = true;
   int shape = ISING_SHAPE_AUTO;
+  uint32_t* d_cl_list = nullptr;  // the cluster path's film list: one cluster, this film
   // asynchronous record copies (ising_read_series_async): records
   // [inflight_lo, inflight_hi) of the ring counters are still being copied
   // on copy_stream until ev_copied
@@ -297,6 +298,14 @@ int ensure_stage(ising* h) {
   return ISING_OK;
 }
 
+// CTAs per cluster of a single film on the cluster path: the most (up to
+// kClusterMaxSize) its layers and shared memory allow, 0 if none.
+uint32_t film_cluster_size(const FilmDesc& d) {
+  for (uint32_t C = kClusterMaxSize; C >= 1; C--)
+    if (cluster_smem_bytes(d, C)) return C;
+  return 0;
+}
+
 // The launch shape of an ising_sweep call: the pinned one, else the
 // autotuner's choice for this film shape and record interval, else the
 // resident kernel up to kResidentAutoSites spins and one word per thread above.
@@ -304,7 +313,9 @@ int resolve_shape(ising* h, uint32_t measure_every) {
   const FilmDesc& d = h->d();
   if (h->shape != ISING_SHAPE_AUTO) return h->shape;
   int s = 0;
-  if (tune_lookup(tune_key(d, measure_every), &s) && (s != ISING_SHAPE_RESIDENT || resident_smem_bytes(d))) return s;
+  if (tune_lookup(tune_key(d, measure_every), &s) && (s != ISING_SHAPE_RESIDENT || resident_smem_bytes(d)) &&
+      (s != ISING_SHAPE_CLUSTER || film_cluster_size(d)))
+    return s;
   const uint64_t sites = (uint64_t)d.Lx * d.Ly * d.Lz;
   return (sites <= kResidentAutoSites && resident_smem_bytes(d)) ? ISING_SHAPE_RESIDENT : ISING_SHAPE_GRID_1;
 }
@@ -559,9 +570,11 @@ int ising_reserve_records(ising* h, uint64_t n_records) {
 int ising_set_shape(ising* h, int shape) {
   clear_error();
   if (!h) return fail(ISING_EINVAL, "NULL handle");
-  if (shape < ISING_SHAPE_AUTO || shape > ISING_SHAPE_GRID_Q) return fail(ISING_EINVAL, "unknown shape %d", shape);
+  if (shape < ISING_SHAPE_AUTO || shape > ISING_SHAPE_CLUSTER) return fail(ISING_EINVAL, "unknown shape %d", shape);
   if (shape == ISING_SHAPE_RESIDENT && !resident_smem_bytes(h->d()))
     return fail(ISING_EINVAL, "film too large for the resident kernel");
+  if (shape == ISING_SHAPE_CLUSTER && !film_cluster_size(h->d()))
+    return fail(ISING_EINVAL, "film too large for the cluster kernel");
   h->shape = shape;
   return ISING_OK;
 }
@@ -593,8 +606,9 @@ int ising_autotune(ising* h, uint32_t measure_every, int* shape) {
   int best = ISING_SHAPE_GRID_1;
   float best_ms = 3.0e38f;
   std::vector<int64_t> drain;
-  for (int cand = ISING_SHAPE_RESIDENT; !rc && cand <= ISING_SHAPE_GRID_Q; cand++) {
+  for (int cand = ISING_SHAPE_RESIDENT; !rc && cand <= ISING_SHAPE_CLUSTER; cand++) {
     if (cand == ISING_SHAPE_RESIDENT && !resident_smem_bytes(d)) continue;
+    if (cand == ISING_SHAPE_CLUSTER && !film_cluster_size(d)) continue;
     s->shape = cand;
     float ms = 3.0e38f;
     for (int rep = 0; !rc && rep < 3; rep++) {  // the first run warms up
@@ -645,6 +659,28 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
   rc = sync_desc(h);
   if (rc) return rc;
   const int shape = resolve_shape(h, measure_every);
+  if (shape == ISING_SHAPE_CLUSTER) {
+    // every sweep of the call in one launch: one cluster holds the film in
+    // distributed shared memory
+    if (!h->d_cl_list) {
+      const uint32_t list[3] = {0u, 1u, 0u};  // cluster 0 sweeps film 0
+      if (dev_alloc(&h->d_cl_list, sizeof list) != cudaSuccess)
+        return fail(ISING_ENOMEM, "cannot allocate the cluster film list");
+      ISG_CK(cudaMemcpy(h->d_cl_list, list, sizeof list, cudaMemcpyHostToDevice));
+    }
+    const uint32_t C = film_cluster_size(d);
+    const bool exact = d.has_never != 0;
+    for (uint64_t done = 0; done < n;) {
+      const uint32_t k = (uint32_t)std::min<uint64_t>(n - done, 4096);
+      ISG_CK(launch_cluster(h->fs.L.films, h->d_cl_list, 1, C, 1, cluster_smem_bytes(d, C),
+                            cluster_threads(d, C, exact, 1), exact, h->fs.pool, h->fs.rec, k, h->fs.stream));
+      done += k;
+    }
+    d.sweep = (uint32_t)(s0 + n);
+    d.rec_next += (uint32_t)nrec;
+    h->rec_written += nrec;
+    return ISING_OK;
+  }
   if (shape == ISING_SHAPE_RESIDENT) {
     const uint32_t smem = resident_smem_bytes(d);
     // small film: every sweep of the call in one launch, planes in shared memory
@@ -772,6 +808,7 @@ int ising_destroy(ising* h) {
   h->fs.release();
   if (h->d_direct) cudaFree(h->d_direct);
   if (h->d_stage) cudaFree(h->d_stage);
+  if (h->d_cl_list) cudaFree(h->d_cl_list);
   delete h;
   return ISING_OK;
 }

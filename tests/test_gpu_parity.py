@@ -55,15 +55,16 @@ def _pair(case, seed=7, replica=3, shape=ig.SHAPE_AUTO):
     return g, o
 
 
-SHAPES = [ig.SHAPE_RESIDENT, ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q]
+SHAPES = [ig.SHAPE_RESIDENT, ig.SHAPE_GRID_1, ig.SHAPE_GRID_2, ig.SHAPE_GRID_Q, ig.SHAPE_CLUSTER]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2", "gridq"])
+@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2", "gridq", "cluster"])
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}-y{c[3]}x{c[4]}-T{c[7]}" for c in CASES])
 def test_sweeps_bit_exact(case, shape):
     """Every launch shape: the resident kernel (the film in shared memory for
-    the whole call) and the grid kernels with one or two words per thread or
-    four threads per word."""
+    the whole call), the grid kernels with one or two words per thread or
+    four threads per word, and the cluster kernel (the film in the
+    distributed shared memory of min(Lx, 8) CTAs for the whole call)."""
     g, o = _pair(case, shape=shape)
     assert np.array_equal(g.get_spins(), o.get_spins()), "initial state differs"
     done = 0
@@ -147,7 +148,7 @@ def test_checkpoint_resume_is_bit_exact():
     h.close()
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2", "gridq"])
+@pytest.mark.parametrize("shape", SHAPES, ids=["resident", "grid1", "grid2", "gridq", "cluster"])
 def test_sweeps_up_to_the_counter_limit_are_bit_exact(shape):
     """The sweep index is the third word of every Philox counter, and
     0xFFFFFFFF is reserved for the initial state's draws.  A film resumed 40
@@ -367,7 +368,8 @@ def test_thermodynamic_integration_from_gpu_records_matches_oracle():
 
 def test_shape_limits_and_switches():
     """The resident kernel is refused for a film it cannot hold; a film can
-    change launch shape in the middle of its chain."""
+    change launch shape (the cluster kernel included) in the middle of its
+    chain."""
     big = ig.Film(64, 64, 32, 1.0, 0.5, 3.0, 1)  # 131072 spins
     with pytest.raises(ig.IsingError) as e:
         big.set_shape(ig.SHAPE_RESIDENT)
@@ -377,7 +379,8 @@ def test_shape_limits_and_switches():
     case = (12, 10, 40, ig.Y_GAPBC, ig.X_FREE, 0.55, 0.0, 3.0, ig.INIT_SLAB_Y, 0.01)
     g, o = _pair(case)
     for shape, n, m in ((ig.SHAPE_RESIDENT, 7, 2), (ig.SHAPE_GRID_2, 5, 3), (ig.SHAPE_GRID_1, 4, 4),
-                        (ig.SHAPE_GRID_Q, 6, 2), (ig.SHAPE_RESIDENT, 11, 1)):
+                        (ig.SHAPE_CLUSTER, 9, 2), (ig.SHAPE_GRID_Q, 6, 2), (ig.SHAPE_CLUSTER, 3, 1),
+                        (ig.SHAPE_RESIDENT, 11, 1)):
         g.set_shape(shape)
         g.sweep(n, m)
         assert np.array_equal(g.read_series(), o.sweep(n, m))
