@@ -273,7 +273,8 @@ int ising_batch_reserve_records(ising_batch *b, uint64_t n_records);
  * fit on the GPU's SMs (C = 1 when the films outnumber the SMs); a film
  * qualifies for C when Lx >= C and a CTA's slab of ceil(Lx / C) layers (two
  * planes of Ly W 32-bit words each, W = ceil(Lz / 64)) plus 24 Lx bytes of
- * tables fits in 200 KiB of shared memory.  EINVAL when none qualifies.
+ * tables fits in 200 KiB of shared memory and the GPU can hold such a
+ * cluster (cudaOccupancyMaxActiveClusters > 0).  EINVAL when none qualifies.
  * RESIDENT is EINVAL for a batch.  Changing it drops the captured graphs. */
 int ising_batch_set_shape(ising_batch *b, int shape);
 int ising_batch_get_shape(ising_batch *b, int *shape);

@@ -299,10 +299,14 @@ int ensure_stage(ising* h) {
 }
 
 // CTAs per cluster of a single film on the cluster path: the most (up to
-// kClusterMaxSize) its layers and shared memory allow, 0 if none.
+// kClusterMaxSize) its layers and shared memory allow and the GPU can hold
+// as one cluster, 0 if none.
 uint32_t film_cluster_size(const FilmDesc& d) {
-  for (uint32_t C = kClusterMaxSize; C >= 1; C--)
-    if (cluster_smem_bytes(d, C)) return C;
+  const bool exact = d.has_never != 0;
+  for (uint32_t C = kClusterMaxSize; C >= 1; C--) {
+    const uint32_t m = cluster_smem_bytes(d, C);
+    if (m && cluster_capacity(C, 1, m, cluster_threads(d, C, exact, 1), exact) > 0) return C;
+  }
   return 0;
 }
 

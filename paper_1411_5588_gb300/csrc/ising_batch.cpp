@@ -142,6 +142,9 @@ int lane_cluster_params(const Lane* b, uint32_t C, uint32_t per_sm, uint32_t* sm
     *smem = std::max(*smem, m);
     *threads = std::max(*threads, cluster_threads(d, C, *exact, per_sm));
   }
+  const int cap = cluster_capacity(C, per_sm, *smem, *threads, *exact);
+  if (cap < 0) return fail(ISING_ECUDA, "cluster occupancy query failed");
+  if (cap == 0) return fail(ISING_EINVAL, "this GPU cannot hold a cluster of %u CTAs of this size", C);
   return ISING_OK;
 }
 
@@ -670,8 +673,7 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
       for (const Lane* l : b->lanes) {
         uint32_t smem = 0, threads = 0;
         bool exact = false;
-        ok = ok && lane_cluster_params(l, C, per_sm, &smem, &threads, &exact) == ISING_OK &&
-             cluster_capacity(C, per_sm, smem, threads, exact) > 0;
+        ok = ok && lane_cluster_params(l, C, per_sm, &smem, &threads, &exact) == ISING_OK;
       }
       clear_error();
       if (ok) cands.push_back({ISING_SHAPE_CLUSTER, C});
