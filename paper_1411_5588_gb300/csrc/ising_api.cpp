@@ -280,6 +280,10 @@ struct ising {
   bool dirty = true;
   int shape = ISING_SHAPE_AUTO;
   uint32_t* d_cl_list = nullptr;  // the cluster path's film list: one cluster, this film
+  // cluster size of this film (film_cluster_size), cached for the table
+  // variant it was found for (cl_exact: 0 fast, 1 exact, -1 none yet)
+  uint32_t cl_size = 0;
+  int cl_exact = -1;
   // asynchronous record copies (ising_read_series_async): records
   // [inflight_lo, inflight_hi) of the ring counters are still being copied
   // on copy_stream until ev_copied
@@ -310,6 +314,17 @@ uint32_t film_cluster_size(const FilmDesc& d) {
   return 0;
 }
 
+// film_cluster_size of the handle's film, looked up once per table variant
+// (the geometry of a handle never changes; its table variant can).
+uint32_t handle_cluster_size(ising* h) {
+  const int exact = h->d().has_never != 0 ? 1 : 0;
+  if (h->cl_exact != exact) {
+    h->cl_size = film_cluster_size(h->d());
+    h->cl_exact = exact;
+  }
+  return h->cl_size;
+}
+
 // The launch shape of an ising_sweep call: the pinned one, else the
 // autotuner's choice for this film shape and record interval, else the
 // resident kernel up to kResidentAutoSites spins and one word per thread above.
@@ -318,7 +333,7 @@ int resolve_shape(ising* h, uint32_t measure_every) {
   if (h->shape != ISING_SHAPE_AUTO) return h->shape;
   int s = 0;
   if (tune_lookup(tune_key(d, measure_every), &s) && (s != ISING_SHAPE_RESIDENT || resident_smem_bytes(d)) &&
-      (s != ISING_SHAPE_CLUSTER || film_cluster_size(d)))
+      (s != ISING_SHAPE_CLUSTER || handle_cluster_size(h)))
     return s;
   const uint64_t sites = (uint64_t)d.Lx * d.Ly * d.Lz;
   return (sites <= kResidentAutoSites && resident_smem_bytes(d)) ? ISING_SHAPE_RESIDENT : ISING_SHAPE_GRID_1;
@@ -577,7 +592,7 @@ int ising_set_shape(ising* h, int shape) {
   if (shape < ISING_SHAPE_AUTO || shape > ISING_SHAPE_CLUSTER) return fail(ISING_EINVAL, "unknown shape %d", shape);
   if (shape == ISING_SHAPE_RESIDENT && !resident_smem_bytes(h->d()))
     return fail(ISING_EINVAL, "film too large for the resident kernel");
-  if (shape == ISING_SHAPE_CLUSTER && !film_cluster_size(h->d()))
+  if (shape == ISING_SHAPE_CLUSTER && !handle_cluster_size(h))
     return fail(ISING_EINVAL, "film too large for the cluster kernel");
   h->shape = shape;
   return ISING_OK;
@@ -672,8 +687,9 @@ int ising_sweep(ising* h, uint64_t n, uint32_t measure_every) {
         return fail(ISING_ENOMEM, "cannot allocate the cluster film list");
       ISG_CK(cudaMemcpy(h->d_cl_list, list, sizeof list, cudaMemcpyHostToDevice));
     }
-    const uint32_t C = film_cluster_size(d);
+    const uint32_t C = handle_cluster_size(h);
     const bool exact = d.has_never != 0;
+    if (C == 0) return fail(ISING_EINVAL, "film too large for the cluster kernel");
     for (uint64_t done = 0; done < n;) {
       const uint32_t k = (uint32_t)std::min<uint64_t>(n - done, 4096);
       ISG_CK(launch_cluster(h->fs.L.films, h->d_cl_list, 1, C, 1, cluster_smem_bytes(d, C),
