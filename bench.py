@@ -424,6 +424,39 @@ def procedures(ig, WL):
     return out
 
 
+def one_field_set(ig, WL, sweeps=1000):
+    """The contact-angle procedure at one surface field (10 films 32x96x64,
+    a record every sweep): too few words per half-sweep to fill the GPU, the
+    case the cluster-resident shape is for.  Autotuned (all shapes) against
+    the faster of the grid shapes GRID_1 and GRID_Q, each pinned."""
+    jobs = WL.contact_angle_set(H1s=(0.3,), n_sweeps=sweeps)["jobs"]
+    att = sum(WL.sites(j) for j in jobs) * sweeps
+
+    def timed(shape=None):
+        b = ig.Batch(jobs)
+        picked = SHAPE_NAMES[b.autotune()] if shape is None else SHAPE_NAMES[shape]
+        if shape is not None:
+            b.set_shape(shape)
+        if b.get_shape() == ig.SHAPE_CLUSTER:
+            picked += f", {b.cluster_size} CTAs per film"
+        b.reserve_records(sweeps + 8)
+        b.sweep(8, True)
+        b.synchronize()
+        for i in range(len(jobs)):
+            b.read_series(i)
+        t0 = time.perf_counter()
+        b.sweep(sweeps, True)
+        b.synchronize()
+        dt = time.perf_counter() - t0
+        b.close()
+        return att / dt / 1e9, picked
+
+    auto, shape = timed()
+    grid = max(timed(ig.SHAPE_GRID_1)[0], timed(ig.SHAPE_GRID_Q)[0])
+    return {"films": len(jobs), "film": [32, 96, 64], "sweeps": sweeps, "autotuned": auto, "shape": shape,
+            "grid_best": grid, "ratio": auto / grid, "unit": UNIT}
+
+
 PROFILE_SETS = ("ti64", "contact_angle", "interface_tension", "line_tension")
 
 
@@ -484,6 +517,10 @@ def headline(extras):
     t = extras.get("t_scan") or {}
     if "attempts_per_ns" in t:
         h["t_scan_40_films"] = {"attempts_per_ns": round(t["attempts_per_ns"], 1), "alu_frac": round(t["alu_frac"], 3)}
+    o = extras.get("one_field_set") or {}
+    if "autotuned" in o:
+        h["contact_angle_one_field"] = {"autotuned": round(o["autotuned"], 1), "grid_best": round(o["grid_best"], 1),
+                                        "ratio": round(o["ratio"], 2), "shape": o["shape"]}
     f = extras.get("film_8") or {}
     if "attempts_per_ns" in f:
         h["film_8"] = {"attempts_per_ns": round(f["attempts_per_ns"], 3)}
@@ -633,7 +670,8 @@ def main():
                          ("serving_capacity", lambda: serving_capacity(ig, WL)),
                          ("film_8", lambda: film_8_run(ig, WL)),
                          ("t_scan", lambda: t_scan_slice(ig, WL)),
-                         ("procedures", lambda: procedures(ig, WL))):
+                         ("procedures", lambda: procedures(ig, WL)),
+                         ("one_field_set", lambda: one_field_set(ig, WL))):
             try:
                 extras[name] = fn()
             except Exception as exc:  # report, never hide the main line
