@@ -457,7 +457,7 @@ def one_field_set(ig, WL, sweeps=1000):
             "grid_best": grid, "ratio": auto / grid, "unit": UNIT}
 
 
-PROFILE_SETS = ("ti64", "contact_angle", "interface_tension", "line_tension")
+PROFILE_SETS = ("ti64", "contact_angle", "interface_tension", "line_tension", "contact_angle_one_field")
 
 
 def profile_set(args):
@@ -473,7 +473,8 @@ def profile_set(args):
     jobs = {"ti64": lambda: WL.ti_batch(n_sweeps=n),
             "contact_angle": lambda: WL.contact_angle_set(n_sweeps=n)["jobs"],
             "interface_tension": lambda: WL.interface_tension_set(n_sweeps=n)["jobs"],
-            "line_tension": lambda: WL.line_tension_set(n_sweeps=n)["jobs"]}[args.profile_set]()
+            "line_tension": lambda: WL.line_tension_set(n_sweeps=n)["jobs"],
+            "contact_angle_one_field": lambda: WL.contact_angle_set(H1s=(0.3,), n_sweeps=n)["jobs"]}[args.profile_set]()
     if args.profile_every is not None:
         jobs = [dict(j, measure_every=args.profile_every) for j in jobs]
     b = ig.Batch(jobs, lanes=args.profile_lanes)
