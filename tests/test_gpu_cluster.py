@@ -235,3 +235,30 @@ def test_autotune_with_cluster_candidates_leaves_the_chains_alone(small):
         calls.append((5, False))
     _check(b, specs, calls)
     b.close()
+
+
+def test_cluster_slab_at_the_shared_memory_limit():
+    """A film whose slab on 8 CTAs needs exactly the 200 KiB a CTA may take
+    (64 x 1588 x 128: 8 layers x 1588 rows x 2 words x 2 planes x 4 B, plus
+    24 B per layer of tables) runs bit-exact; one row more is refused for 8
+    CTAs, and then for every size (fewer CTAs hold larger slabs): EINVAL,
+    and the batch stays on the grid kernels."""
+    sp = dict(Lx=64, Ly=1588, Lz=128, y_mode=ig.Y_GAPBC, x_mode=ig.X_FREE, H1=0.5, H=0.0, T=3.0, seed=11,
+              replica=0, init_kind=ig.INIT_SLAB_Y, flip_p=0.01, measure_every=1)
+    b = ig.Batch([sp], lanes=1)
+    b.set_cluster_size(8)
+    b.set_shape(ig.SHAPE_CLUSTER)
+    assert b.cluster_size == 8
+    b.sweep(3, False)
+    _check(b, [sp], [(3, False)])
+    b.close()
+    big = dict(sp, Ly=1589)
+    b = ig.Batch([big], lanes=1)
+    with pytest.raises(ig.IsingError) as e:
+        b.set_cluster_size(8)
+    assert e.value.status == ig.EINVAL
+    with pytest.raises(ig.IsingError) as e:
+        b.set_shape(ig.SHAPE_CLUSTER)
+    assert e.value.status == ig.EINVAL
+    assert b.cluster_size == 0 and b.get_shape() == ig.SHAPE_GRID_1
+    b.close()
