@@ -17,6 +17,8 @@ Usage (each configuration writes its own file ``digests_<name>.json``):
   python tests/golden/make_config_digests.py film_46m            # 2000 sweeps, a record every 10
   python tests/golden/make_config_digests.py ti_batch [sweeps]   # 64 films, 5000 sweeps, a record every sweep
   python tests/golden/make_config_digests.py t_scan_ends         # T = 1.5 and 4.4 films, 10^4 sweeps
+  python tests/golden/make_config_digests.py contact_angle_one_field [sweeps]
+                                          # the contact-angle set at H1 = 0.3: 10 films, 5000 sweeps
 """
 from __future__ import annotations
 
@@ -83,6 +85,11 @@ def main(argv):
         jobs = WL.t_scan_40()
         todo = [(i, jobs[i], jobs[i]["n_sweeps"], ncpu) for i in (0, len(jobs) - 1)]
         desc = "40-film temperature scan: the T = 1.5 and T = 4.4 films, full run (a record every sweep)"
+    elif name == "contact_angle_one_field":
+        n = int(argv[2]) if len(argv) > 2 else 5000
+        jobs = WL.contact_angle_set(H1s=(0.3,), n_sweeps=n)["jobs"]
+        todo = [(i, j, n, 1) for i, j in enumerate(jobs)]
+        desc = f"contact-angle set at H1 = 0.3 (10 films 32x96x64), every film, {n} sweeps with a record every sweep"
     else:
         raise SystemExit(f"unknown configuration {name!r}")
     t0 = time.time()
