@@ -14,7 +14,11 @@ final spins: a bit-exact match over the whole run.
     CUDA graphs, a record every sweep;
   - the 40-film temperature scan: all 40 films in one batch for 10^4 sweeps
     with a record every sweep, the coldest (T = 1.5) and hottest (T = 4.4)
-    against the oracle's digests of their whole runs.
+    against the oracle's digests of their whole runs;
+  - the contact-angle set at one field (10 films 32x96x64) on the
+    cluster-resident shape, 8 CTAs per film, in one call of 5000 sweeps with a
+    record every sweep (two launches of 4096 and 904 sweeps per lane), every
+    film against the oracle's digests.
 """
 import hashlib
 import json
@@ -142,4 +146,21 @@ def test_temperature_scan_full_run():
         if recs is not None:
             assert recs.shape == (n, 5 + j["Lx"]), i
             assert np.array_equal(recs[-1], o.measure()), i
+    b.close()
+
+
+def test_contact_angle_one_field_full_run_on_clusters():
+    d = digests("contact_angle_one_field")
+    n = d["films"][0]["n_sweeps"]
+    assert n > 4096  # the call spans two cluster launches
+    jobs = stored_jobs(d, WL.contact_angle_set(H1s=(0.3,), n_sweeps=n)["jobs"])
+    assert len(jobs) == 10
+    b = ig.Batch(jobs)
+    b.set_cluster_size(8)
+    b.set_shape(ig.SHAPE_CLUSTER)
+    b.reserve_records(n)
+    b.sweep(n, True)
+    for e in d["films"]:
+        i = e["index"]
+        check_film(e, b.read_series(i), b.get_spins(i), f"one-field contact-angle film {i} on clusters")
     b.close()
