@@ -664,9 +664,7 @@ int ising_batch_autotune(ising_batch* b, int* shape) {
   std::vector<std::pair<int, uint32_t>> cands = {
       {ISING_SHAPE_GRID_1, 0}, {ISING_SHAPE_GRID_2, 0}, {ISING_SHAPE_GRID_Q, 0}};
   {
-    const size_t nf = b->jobs.size();
     const size_t n_sm = (size_t)std::max(1, b->lanes[0]->fs.n_sm);
-    (void)nf;
     for (uint32_t C = 1; C <= kClusterMaxSize && C * b->lanes.size() <= n_sm; C++) {
       const uint32_t per_sm = 1;
       bool ok = true;
